@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""ChFSI filter throughput on one GB300 (spinor-DOF x vectors x degree / s).
+
+Workload (default, N = 1): the 16^3-cell, p = 6 (n_q = 8) periodic mesh with
+884,736 FE nodes, 64 atoms with 18 SOC projectors each, a block of 256
+two-component spinors, Chebyshev degree 20, on each of the 4 k-points of a
+2x2x1 Monkhorst-Pack grid.  One timed step = the degree-20 filter of all four
+k-point blocks (each degree = one H.X with its fused recurrence update), inputs
+resident in HBM; value = 884736 * 256 * 20 * 4 / step time.  The mixed path
+(complex64 filter, FP64 Gram/Rayleigh-Ritz) is timed; the FP64 filter and the
+Ritz-value difference between the two paths are reported beside it.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the only place, with the ``cpu_baseline`` leg,
+where this script runs the oracle).
+
+Under torchrun (N > 1) every rank runs its own copy of the workload on its own
+GPU (weak scaling, no collective in the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ChFSI filter spinor-DOF·vectors·degree/s, mixed vs FP64 at 1e-6 Ha, 1 GB300"
+UNIT = "spinor-DOF*vectors*degree/s"
+WORKLOAD = ("16x16x16 periodic cells, p=6, nq=8 (884,736 nodes), 64 atoms x 18 SOC projectors, "
+            "256 spinor vectors, Chebyshev degree 20, 4 k-points (2x2x1 MP)")
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (shared with the gloo tests)
+# ----------------------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return rank, world
+
+
+def dist_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def dist_max(x: float, device="cpu") -> float:
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def dist_sum(x: float, device="cpu") -> float:
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+    return x
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[2][1:]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def flops_per_cell_vector(p: int, nq: int, kpt: bool) -> int:
+    """Arithmetic (FMA = 2 flop) of the matrix-free cell apply for one cell and
+    one two-component vector, counted from its contraction structure:
+    kinetic/k part 7 one-dimensional n x n contractions (complex G when k != 0),
+    3 + 3 interpolation/test contractions n <-> nq, and the pointwise 2x2 spin
+    operator at the nq^3 Gauss points."""
+    n, q = p + 1, nq
+    g = 4 * n * n if kpt else 2 * n * n          # FMA per output pencil point of G
+    kin = 2 * n * n * (8 * n * n + 3 * g)
+    interp = 8 * (n ** 3 * q + n * n * q * q + n * q ** 3)
+    pointwise = 16 * q ** 3
+    return 2 * (kin + interp + pointwise)
+
+
+def build_contexts(g, prob, ks, prec):
+    import torch
+    ctxs = []
+    for k in ks:
+        c = g.Context(torch.cuda.current_device())
+        c.set_problem(prob.with_(k=k))
+        c.set_precision(prec)
+        ctxs.append(c)
+    return ctxs
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import synthetic as syn
+    import paper_2410_02754_gb300 as g
+
+    rank, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "gloo")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    ge.build()
+    cfg = syn.CONFIGS[args.config]
+    nvec, degree = cfg["nvec"], cfg["degree"]
+    prob = syn.config(args.config, seed=0)
+    ks = syn.mp_kpoints(*cfg["kgrid"], prob.box)
+    if args.kpoints:
+        ks = ks[:args.kpoints]
+    M = prob.nnodes
+    units_per_step = M * nvec * degree * len(ks)
+
+    # ---- contexts, blocks, bounds (outside the timed region)
+    ctx32 = build_contexts(g, prob, ks, g.FP32)
+    X0 = syn.random_block(M, nvec, 0)
+    v0 = torch.from_numpy(syn.random_start(M, 0)).cuda()
+    bounds = []
+    X32 = []
+    for c in ctx32:
+        lo, hi = c.lanczos_bounds(v0, cfg["lanczos"])
+        X = torch.from_numpy(X0).to(torch.complex64).cuda()
+        c.cholgs(X)
+        ritz = c.rayleigh_ritz(X)
+        bounds.append((float(ritz[-1]), hi, lo))
+        X32.append(X)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for c, X, (lT, lmax, lmin) in zip(ctx32, X32, bounds):
+            c.filter(X, degree, lT, lmax, lmin)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for c in ctx32:
+        c.set_timing(True)
+    dist_barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    dist_barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = dist_max(ms_total, device="cuda" if world > 1 else "cpu")
+    ms_step = ms_total / args.steps
+    value = dist_sum(units_per_step, device="cuda" if world > 1 else "cpu") / (ms_step / 1e3)
+
+    # ---- per-kernel-family device time (CUDA events around every launch)
+    fams = {}
+    for c in ctx32:
+        for name, (t, n) in c.timing().items():
+            a = fams.setdefault(name, [0.0, 0])
+            a[0] += t
+            a[1] += n
+        c.set_timing(False)
+    # kernels per family launch: local 1, nonlocal 3 (project, couple, expand), epilogue 1
+    launches = fams["hx_local"][1] + 3 * fams["nonlocal"][1] + fams["cheb"][1]
+    launches += (degree % 2) * len(ks) * args.steps      # final block copy for odd degree
+    tot = sum(v[0] for v in fams.values()) or 1.0
+    kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1],
+                   "avg_ms": round(v[0] / v[1], 4) if v[1] else None,
+                   "share": round(v[0] / tot, 4)} for k, v in fams.items() if v[1]}
+    loc = fams["hx_local"]
+    avg_local_ms = loc[0] / loc[1]
+    kpt = any(abs(x) > 0 for k in ks for x in k)
+    flops_launch = flops_per_cell_vector(prob.p, prob.nq, kpt) * prob.ncells * nvec
+    clocks = clk.summary()
+    peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
+    roofline = {"bound": "alu", "kernel": "hx_local_kernel<float,7,8,kpt>",
+                "achieved": round(flops_launch / (avg_local_ms / 1e3) / 1e12, 3),
+                "peak": round(peak_alu, 2), "unit": "TFLOP/s",
+                "frac": round(flops_launch / (avg_local_ms / 1e3) / 1e12 / peak_alu, 4),
+                "traffic": None,
+                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",
+                "flops_per_launch": flops_launch}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "config": args.config, "nodes": M, "nvec": nvec,
+                      "degree": degree, "kpoints": len(ks), "precision": "FP32 filter (complex64)",
+                      "l2": "inputs larger than L2 (3.6 GB per k-point block, 126 MB L2)",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+           "kernels": kernels}
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    if not args.no_e2e:
+        host = [torch.empty(X.shape, dtype=X.dtype, pin_memory=True) for X in X32]
+        for h, X in zip(host, X32):
+            h.copy_(X)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nrep = max(1, min(args.steps, 2))
+        e0.record(stream)
+        for _ in range(nrep):
+            for c, X, h, (lT, lmax, lmin) in zip(ctx32, X32, host, bounds):
+                X.copy_(h, non_blocking=True)
+                c.filter(X, degree, lT, lmax, lmin)
+                h.copy_(X, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = dist_max(e0.elapsed_time(e1), device="cuda" if world > 1 else "cpu") / nrep
+        nbytes = sum(X.numel() * X.element_size() for X in X32)
+        out["e2e"] = {"value": dist_sum(units_per_step, "cuda" if world > 1 else "cpu") / (ms_e2e / 1e3),
+                      "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                      "ms_per_step": ms_e2e}
+
+    # ---- FP64 filter and accuracy of the mixed path at the same inputs (k-point 0)
+    if not args.no_fp64 and rank == 0:
+        c64 = build_contexts(g, prob, ks[:1], g.FP64)[0]
+        c32 = ctx32[0]
+        lo, hi = c64.lanczos_bounds(v0, cfg["lanczos"])
+        Xa = torch.from_numpy(X0).cuda()
+        c64.cholgs(Xa)
+        r0 = c64.rayleigh_ritz(Xa)
+        Xb = torch.from_numpy(X0).to(torch.complex64).cuda()
+        c32.cholgs(Xb)
+        c32.rayleigh_ritz(Xb)
+        lT = float(r0[-1])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c64.filter(Xa, degree, lT, hi, lo)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        c32.filter(Xb, degree, lT, hi, lo)
+        c64.cholgs(Xa)
+        ritz64 = c64.rayleigh_ritz(Xa)
+        c32.cholgs(Xb)
+        ritz32 = c32.rayleigh_ritz(Xb)
+        half = nvec // 2
+        out["fp64"] = {"value": M * nvec * degree / (ms64 / 1e3), "unit": UNIT,
+                       "ms_per_filter": ms64, "mixed_over_fp64":
+                           value / (M * nvec * degree / (ms64 / 1e3))}
+        out["accuracy"] = {"ritz_maxdiff_mixed_vs_fp64_ha_lower_half": float(np.abs(ritz32 - ritz64)[:half].max()),
+                           "ritz_maxdiff_mixed_vs_fp64_ha_all": float(np.abs(ritz32 - ritz64).max()),
+                           "target_ha": 1e-6, "cycle": "cycle0 + 1 x (filter, CholGS, RR), k-point 0"}
+        c64.close()
+
+    # ---- CPU baseline: the oracle as it stands, bounded sample (rank 0, N = 1)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_sample(args, prob, ks[0], budget_s=args.cpu_budget)
+
+    for c in ctx32:
+        c.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def cpu_sample(args, prob, k, budget_s=20.0, nv=2):
+    """One recurrence step (H.X by element-by-element quadrature + the sigma-scaled
+    update) of the FP64 oracle on an nv-vector sample of the workload."""
+    import numpy as np
+
+    import synthetic as syn
+    from oracle import fe
+
+    d = fe.Discretisation(prob.with_(k=k))
+    M = d.mesh.nnodes
+    X = syn.random_block(M, nv, 1)
+    Xp = syn.random_block(M, nv, 2)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        Y = d.apply_htilde(X)
+        _ = 0.1 * (Y - 3.0 * X) - 0.5 * Xp
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 50:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": M * nv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} x one recurrence step (FP64 O1b H.X + update), {nv} vectors, "
+                      f"full mesh ({M} nodes), k-point 0; numpy/BLAS threads over all cores",
+            "seconds": round(dt * reps, 2)}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on this arm's config/metric, rank 0 only."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synthetic as syn
+    cfg = syn.CONFIGS[args.config]
+    prob = syn.config(args.config, seed=0)
+    ks = syn.mp_kpoints(*cfg["kgrid"], prob.box)
+    budget = max(2.0, min(30.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_sample(args, prob, ks[0], budget_s=budget / 4)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_sample(args, prob, ks[0], budget_s=budget))
+    wall = time.perf_counter() - t0
+    v = sum(x["value"] for x in vals) / len(vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "config": args.config},
+           "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbchfsi", choices=["gbchfsi", "reference"])
+    ap.add_argument("--config", default="c1")
+    ap.add_argument("--kpoints", type=int, default=0, help="use only the first K k-points")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * gbchfsi -- Chebyshev-filtered subspace iteration for two-component spinors
+ * under the finite-element Kohn-Sham Hamiltonian with noncollinear B_xc and
+ * spin-orbit-coupled nonlocal projectors, on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI.  Plain pointers and sizes only.  Every call returns a gbc_status; no
+ * C++ exception crosses this boundary.  A context is not thread-safe: calls on
+ * one context must not overlap (they share its workspaces).  Device work is
+ * enqueued on the caller's CUDA stream (``void* stream`` = cudaStream_t, NULL
+ * = the legacy default stream); a call returns once its work is enqueued
+ * unless its description says it reads a result back to the host.
+ *
+ * Discretisation (paper: Sec. III.A, Eqs. FEWfns, GHEP, FEHloc, FEHnloc, CMat,
+ * OvlapMap, cellIntegrals; Sec. III.B.2 for M_D):
+ *   - structured mesh of ncell[0] x ncell[1] x ncell[2] rectangular cells of
+ *     edges h[0..2] (bohr), cell e = (cz*ny + cy)*nx + cx;
+ *   - tensor-product Lagrange basis of degree p on GLL nodes (n_p = p + 1 per
+ *     direction), Gauss-Legendre quadrature with nq points per direction,
+ *     point q = (qz*nq + qy)*nq + qx;
+ *   - per direction either periodic (n*p free nodes) or homogeneous Dirichlet
+ *     on both faces (n*p - 1 free nodes); free node I = (gz*Ny + gy)*Nx + gx;
+ *   - H^k = H^loc + H^nloc on the free nodes, DOF index 2I + alpha
+ *     (alpha = 0 spin up, 1 spin down), Pauli matrices in the standard
+ *     representation; the overlap is the GLL-lumped diagonal mass M_D.
+ *
+ * Spinor blocks ("X", "Y"): caller-owned device memory, layout
+ *   [M][2][ldx] complex, real and imaginary parts interleaved, vector index
+ *   fastest: element (I, alpha, v) at complex offset (I*2 + alpha)*ldx + v.
+ *   complex128 (double2) in GBC_FP64, complex64 (float2) in every other
+ *   precision.  Columns nvec..ldx-1 are never read; outputs may overwrite them.
+ */
+#ifndef GBCHFSI_H
+#define GBCHFSI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbc_ctx gbc_ctx;   /* opaque, owned by the library */
+
+typedef enum {
+  GBC_OK = 0,
+  GBC_EINVAL = 1,        /* bad argument (null pointer, size, inconsistent layout)      */
+  GBC_ENOMEM = 2,        /* device or host allocation failed                            */
+  GBC_ECUDA = 3,         /* a CUDA runtime call failed (text in gbc_last_error)          */
+  GBC_ESTATE = 4,        /* call out of order (e.g. apply before set_mesh/set_fields)   */
+  GBC_ENOTPD = 5,        /* Cholesky met a non-positive pivot (overlap not positive def.) */
+  GBC_ETIMEOUT = 6,      /* an iteration cap was reached (eigensolver did not converge)  */
+  GBC_EUNSUPPORTED = 7   /* valid request this build does not implement (p, nq, npj)     */
+} gbc_status;
+
+typedef enum {
+  GBC_FP64 = 0,          /* complex128 blocks, FP64 arithmetic everywhere               */
+  GBC_FP32 = 1           /* complex64 blocks, FP32 arithmetic in H.X and the filter;
+                            Gram matrices accumulated in FP64                           */
+} gbc_precision;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device ``device_ordinal``.  *out is NULL on error. */
+gbc_status gbc_create(gbc_ctx** out, int device_ordinal);
+/* Release the context and all library-owned device memory.  NULL-safe. */
+void gbc_destroy(gbc_ctx* ctx);
+/* Text of the last error on this context; valid until the next call on it. */
+const char* gbc_last_error(const gbc_ctx* ctx);
+/* Library version string (static storage). */
+const char* gbc_version(void);
+
+/* ---- problem definition (host inputs are copied; nothing is retained) --- */
+
+/* Mesh and FE order (Sec. III.A).  p in [2, 7]; this build requires
+ * nq == p + 2 (GBC_EUNSUPPORTED otherwise).  periodic[d] != 0 selects a
+ * periodic direction, 0 homogeneous Dirichlet on both faces.  Resets fields,
+ * projectors and the k-point. */
+gbc_status gbc_set_mesh(gbc_ctx* ctx, const int ncell[3], const double h[3], int p, int nq,
+                        const int periodic[3]);
+
+/* Bloch wave vector k (Cartesian, bohr^-1) of Eqs. eigenProbPer / FEHloc:
+ * adds -i k.grad and |k|^2/2 to the local operator and the Bloch phases
+ * e^{-ik.(r - L)} to the projectors (Eq. HnlocPeriodic).  Default 0. */
+gbc_status gbc_set_kpoint(gbc_ctx* ctx, const double k[3]);
+
+/* Quadrature-point fields V_eff and B_xc = (bx, by, bz) in Ha (Eq. FEHloc),
+ * host FP64 arrays of E*nq^3 values each, layout [cell][qz][qy][qx]. */
+gbc_status gbc_set_fields(gbc_ctx* ctx, const double* veff, const double* bx,
+                          const double* by, const double* bz);
+
+/* Atom-centred nonlocal projectors (Eqs. nlOP, CMat, FEHnloc, HnlocPeriodic).
+ * natoms atoms; atom a has npj[a] scalar projectors p_chi (npj[a] <= 32) and a
+ * support of nsupp[a] (cell, image) entries: supp_cell[s] is a cell index and
+ * supp_img[3s..3s+2] the integer lattice image shift n (L = n * box length per
+ * direction) whose copy of the projector overlaps that cell.
+ * pvals holds p_chi(r_q - L - R_a) at the quadrature points of each entry,
+ * layout [entry][q][chi], entries of all atoms concatenated in atom order.
+ * delta holds each atom's Hermitian 2npj x 2npj coupling matrix
+ * Delta_{2chi+alpha, 2chi'+beta} = D^{chi chi'}_{alpha beta}, complex128
+ * row-major, concatenated in atom order.
+ * The library forms P_{I chi} = sum_(e,L) sum_q w_q J N_I(r_q) e^{-ik.(r_q - L)}
+ * p_chi(r_q - L - R_a) on the device and applies
+ * H^nloc = sum_a (P_a x I2) Delta_a (P_a x I2)^H.  natoms = 0 removes them. */
+gbc_status gbc_set_projectors(gbc_ctx* ctx, int natoms, const int* npj, const int* nsupp,
+                              const int* supp_cell, const int* supp_img, const double* pvals,
+                              const double* delta);
+
+/* Arithmetic path for the block calls below.  Default GBC_FP64. */
+gbc_status gbc_set_precision(gbc_ctx* ctx, gbc_precision prec);
+
+/* Number M of free FE nodes (spinor DOFs per vector = 2M). */
+gbc_status gbc_get_nnodes(const gbc_ctx* ctx, long long* nnodes);
+
+/* Copy M_D (length M, FP64) to host memory ``md``.  Synchronous. */
+gbc_status gbc_get_mass(gbc_ctx* ctx, double* md);
+
+/* ---- the hot path -------------------------------------------------------- */
+
+/* Y = H^k X (Sec. IV.B.2: cell-level apply + nonlocal + assembly).
+ * X, Y: distinct device blocks [M][2][ldx], nvec <= ldx.  Y is overwritten. */
+gbc_status gbc_apply_h(gbc_ctx* ctx, const void* X, void* Y, int nvec, int ldx, void* stream);
+
+/* Spectrum bounds of M_D^-1 H by ``steps`` steps of generalised Lanczos in
+ * the M_D inner product with full reorthogonalisation (Sec. III.B.2).
+ * v0: device start spinor [M][2] complex128 (not modified).  On return
+ * (synchronous) *lmin = smallest Ritz value of T_steps and
+ * *lmax = largest Ritz value + |beta_steps|.  Always FP64.  steps in [1, 64]. */
+gbc_status gbc_lanczos_bounds(gbc_ctx* ctx, const void* v0, int steps, double* lmin,
+                              double* lmax, void* stream);
+
+/* In-place Chebyshev filter of degree ``degree`` on M_D^-1 H (Eq. chebfilt),
+ * sigma-scaled: X <- T_m((H~ - c)/e) X / T_m((lmin - c)/e) with
+ * c = (lmax + lT)/2, e = (lmax - lT)/2.  Requires lmin < lT < lmax, degree >= 1.
+ * Each recurrence step is one H.X with the recurrence fused into the
+ * assembly epilogue.  Uses library-owned workspace of two blocks. */
+gbc_status gbc_filter(gbc_ctx* ctx, void* X, int nvec, int ldx, int degree, double lT,
+                      double lmax, double lmin, void* stream);
+
+/* Cholesky-Gram-Schmidt in the M_D inner product: S = X^H M_D X accumulated in
+ * FP64, S = L L^H, X <- X L^-H.  GBC_ENOTPD if S is not positive definite
+ * (X is then left unchanged).  Synchronous (reads the pivot status).
+ * nvec <= 512. */
+gbc_status gbc_cholgs(gbc_ctx* ctx, void* X, int nvec, int ldx, void* stream);
+
+/* Rayleigh-Ritz for an M_D-orthonormal block (Sec. III.B.2): Hp = X^H H X
+ * accumulated in FP64, Hp Q = Q Lambda by a Jacobi eigensolver on the device,
+ * X <- X Q.  ritz: host array of nvec doubles, ascending.  Synchronous.
+ * nvec <= 512.  GBC_ETIMEOUT if the eigensolver hits its sweep cap. */
+gbc_status gbc_rayleigh_ritz(gbc_ctx* ctx, void* X, int nvec, int ldx, double* ritz,
+                             void* stream);
+
+/* ---- tracing -------------------------------------------------------------- */
+
+/* Kernel families for gbc_get_timing. */
+enum {
+  GBC_FAM_HX_LOCAL = 0,   /* cell-level local apply + assembly            */
+  GBC_FAM_NONLOCAL = 1,   /* C = P^H X, C' = Delta C, Y += P C'            */
+  GBC_FAM_CHEB = 2,       /* fused Chebyshev recurrence epilogue           */
+  GBC_FAM_GRAM = 3,       /* FP64-accumulated Gram matrices                */
+  GBC_FAM_ROTATE = 4,     /* block rotation X <- X Q                       */
+  GBC_FAM_DENSE = 5       /* small dense Cholesky / eigensolver            */
+};
+
+/* Enable (1) or disable (0) per-family timing: every later launch of a family
+ * is bracketed by CUDA events recorded on the launch stream.  Synchronises the
+ * device and clears the recorded launches. */
+gbc_status gbc_set_timing(gbc_ctx* ctx, int enable);
+/* Total device time (ms, summed over launches) and launch count of ``family``
+ * since the last gbc_set_timing.  Waits for the recorded events. */
+gbc_status gbc_get_timing(gbc_ctx* ctx, int family, double* total_ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBCHFSI_H */

@@ -222,7 +222,7 @@ class Discretisation:
         return P
 
     # ---- form O1b: element-by-element quadrature apply
-    def apply_local(self, X: np.ndarray, chunk: int = 64) -> np.ndarray:
+    def apply_local(self, X: np.ndarray, chunk: int = 64, cells=None) -> np.ndarray:
         """Y = H^loc X cell by cell (Eq. FEHloc, Eq. cellIntegrals).
 
         X[M][2][nv] complex.  For each cell: u, grad u at the Gauss points by
@@ -236,15 +236,21 @@ class Discretisation:
         k = self.k
         k2 = 0.5 * float(k @ k)
         W = tab.W
-        for c0 in range(0, mesh.ncells, chunk):
-            cells = np.arange(c0, min(mesh.ncells, c0 + chunk))
+        all_cells = np.arange(mesh.ncells) if cells is None else np.asarray(cells)
+        for c0 in range(0, len(all_cells), chunk):
+            cells = all_cells[c0:c0 + chunk]
             idx = mesh.cell_nodes[cells]                        # [C, n]
             Xc = Xp[np.where(idx >= 0, idx, M)]                 # [C, n, 2, nv]
-            U = np.einsum("iq,ciav->cqav", tab.N3, Xc)
-            G = [np.einsum("iq,ciav->cqav", tab.D3[d], Xc) for d in range(3)]
+            C = len(cells)
+            Xm = Xc.reshape(C, Xc.shape[1], 2 * nv)
+            # u and grad u at the Gauss points (library matmul, full 3-D tables)
+            U = (tab.N3.T @ Xm).reshape(C, -1, 2, nv)
+            G = [(tab.D3[d].T @ Xm).reshape(C, -1, 2, nv) for d in range(3)]
+
+            def test(B, F):            # sum_q B[i, q] F[c, q, a, v]
+                return (B @ F.reshape(C, F.shape[1], 2 * nv)).reshape(C, B.shape[0], 2, nv)
             # kinetic: 1/2 int grad N_I . grad u
-            Yc = 0.5 * sum(np.einsum("iq,cqav->ciav", tab.D3[d], W[None, :, None, None] * G[d])
-                           for d in range(3))
+            Yc = 0.5 * sum(test(tab.D3[d], W[None, :, None, None] * G[d]) for d in range(3))
             # -i int N_I k . grad u
             kg = sum(k[d] * G[d] for d in range(3))
             # |k|^2/2 + V_eff, and B_xc . sigma
@@ -255,7 +261,7 @@ class Discretisation:
             pt = -1j * kg + (k2 + V) * U
             pt[:, :, 0, :] += Bz * U[:, :, 0, :] + (Bx - 1j * By) * U[:, :, 1, :]
             pt[:, :, 1, :] += (Bx + 1j * By) * U[:, :, 0, :] - Bz * U[:, :, 1, :]
-            Yc = Yc + np.einsum("iq,cqav->ciav", tab.N3, W[None, :, None, None] * pt)
+            Yc = Yc + test(tab.N3, W[None, :, None, None] * pt)
             ok = idx >= 0
             np.add.at(Y, idx[ok], Yc[ok])
         return Y
@@ -274,6 +280,13 @@ class Discretisation:
     def apply_h(self, X: np.ndarray) -> np.ndarray:
         """H^k X (form O1b): local element-by-element + nonlocal."""
         return self.apply_local(X) + self.apply_nonlocal(X)
+
+    def apply_h_rows(self, X: np.ndarray, nodes) -> np.ndarray:
+        """(H^k X)[nodes] only: the element loop runs over the cells that touch
+        the requested nodes (the only cells contributing to those rows)."""
+        nodes = np.asarray(nodes)
+        cells = np.nonzero(np.isin(self.mesh.cell_nodes, nodes).any(axis=1))[0]
+        return (self.apply_local(X, cells=cells) + self.apply_nonlocal(X))[nodes]
 
     def apply_htilde(self, X: np.ndarray) -> np.ndarray:
         """M_D^-1 H X."""

@@ -1,0 +1,326 @@
+// Block kernels of the ChFSI cycle: the fused Chebyshev recurrence epilogue,
+// M_D-weighted Gram matrices with FP64 accumulation, block rotation X <- X Q,
+// and the FP64 vector helpers of the Lanczos bound estimate.
+//
+// Paper: Eq. chebfilt (three-term recurrence on M_D^-1 H, scaled), Sec. III.B.2
+// (Rayleigh-Ritz: X^H H X, X^H M X, U = X Q).
+#include <type_traits>
+
+#include "gbc_internal.h"
+
+namespace {
+
+// Xout = a (M_D^-1 Y - c Xcur) - b Xprev ; Y <- 0
+// (Xout may alias Xprev; Xprev may be null when b == 0)
+template <typename T>
+__global__ void k_cheb_step(cplx<T>* __restrict__ Y, const cplx<T>* Xcur, const cplx<T>* Xprev,
+                            cplx<T>* Xout, const T* __restrict__ invmd, long long rows, int nvec,
+                            int ldx, T a, T cshift, T b) {
+  const long long n = rows * (long long)nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nvec;
+    const int v = (int)(i - r * nvec);
+    const long long o = r * ldx + v;
+    const T w = invmd[r >> 1];
+    const cplx<T> y = Y[o];
+    const cplx<T> x = Xcur[o];
+    cplx<T> out;
+    out.x = a * (w * y.x - cshift * x.x);
+    out.y = a * (w * y.y - cshift * x.y);
+    if (Xprev) {
+      const cplx<T> xp = Xprev[o];
+      out.x -= b * xp.x;
+      out.y -= b * xp.y;
+    }
+    Xout[o] = out;
+    Y[o] = cmake<cplx<T>>(0, 0);
+  }
+}
+
+// S[i][j] += sum_rows w(row) conj(X[row][i]) Y[row][j], FP64 accumulation.
+// Block: 32 x 32 tile of S, 256 threads with 2 x 2 outputs each; rows staged
+// 32 at a time; the grid's y dimension splits the rows into chunks.
+constexpr int GT = 32;
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gram(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ Yb, const double* __restrict__ md,
+       long long rows, int nvec, int ldx, long long rows_per_chunk, double2* __restrict__ S) {
+  __shared__ double2 xs[GT][GT + 1];
+  __shared__ double2 ys[GT][GT + 1];
+  const int ntile = (nvec + GT - 1) / GT;
+  const int ti = blockIdx.x % ntile, tj = blockIdx.x / ntile;
+  const int i0 = ti * GT, j0 = tj * GT;
+  const long long r0 = blockIdx.y * rows_per_chunk;
+  const long long r1 = min(rows, r0 + rows_per_chunk);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double2 acc[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0, 0);
+  for (long long rb = r0; rb < r1; rb += GT) {
+    for (int t = threadIdx.x; t < GT * GT; t += 256) {
+      const int rr = t / GT, cc = t % GT;
+      const long long r = rb + rr;
+      double2 xv = make_double2(0, 0), yv = make_double2(0, 0);
+      if (r < r1) {
+        const double w = md ? md[r >> 1] : 1.0;
+        if (i0 + cc < nvec) {
+          const cplx<T> t1 = X[r * ldx + i0 + cc];
+          xv = make_double2((double)t1.x * w, (double)t1.y * w);
+        }
+        if (j0 + cc < nvec) {
+          const cplx<T> t2 = Yb[r * ldx + j0 + cc];
+          yv = make_double2((double)t2.x, (double)t2.y);
+        }
+      }
+      xs[rr][cc] = xv;
+      ys[rr][cc] = yv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < GT; ++rr) {
+      const double2 x0 = xs[rr][2 * tx], x1 = xs[rr][2 * tx + 1];
+      const double2 y0 = ys[rr][2 * ty], y1 = ys[rr][2 * ty + 1];
+      // conj(x) * y
+      acc[0][0].x += x0.x * y0.x + x0.y * y0.y;
+      acc[0][0].y += x0.x * y0.y - x0.y * y0.x;
+      acc[0][1].x += x0.x * y1.x + x0.y * y1.y;
+      acc[0][1].y += x0.x * y1.y - x0.y * y1.x;
+      acc[1][0].x += x1.x * y0.x + x1.y * y0.y;
+      acc[1][0].y += x1.x * y0.y - x1.y * y0.x;
+      acc[1][1].x += x1.x * y1.x + x1.y * y1.y;
+      acc[1][1].y += x1.x * y1.y - x1.y * y1.x;
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + 2 * tx + a, j = j0 + 2 * ty + b;
+      if (i < nvec && j < nvec) {
+        atomicAdd(&S[(size_t)i * nvec + j].x, acc[a][b].x);
+        atomicAdd(&S[(size_t)i * nvec + j].y, acc[a][b].y);
+      }
+    }
+}
+
+// Out[row][j] = sum_i X[row][i] Q[i][j]; 64 x 64 output tile, K-steps of 16.
+constexpr int RT = 64, KT = 16;
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_rotate(const cplx<T>* __restrict__ X, const double2* __restrict__ Q, cplx<T>* __restrict__ Out,
+         long long rows, int nvec, int ldx) {
+  using C = cplx<T>;
+  __shared__ C xs[RT][KT + 1];
+  __shared__ C qs[KT][RT + 1];
+  const int ntj = (nvec + RT - 1) / RT;
+  const long long r0 = (long long)(blockIdx.x / ntj) * RT;
+  const int j0 = (blockIdx.x % ntj) * RT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  C acc[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) acc[a][b] = cmake<C>(0, 0);
+  for (int k0 = 0; k0 < nvec; k0 += KT) {
+    for (int t = threadIdx.x; t < RT * KT; t += 256) {
+      const int rr = t / KT, kk = t % KT;
+      const long long r = r0 + rr;
+      C v = cmake<C>(0, 0);
+      if (r < rows && k0 + kk < nvec) v = X[r * ldx + k0 + kk];
+      xs[rr][kk] = v;
+    }
+    for (int t = threadIdx.x; t < KT * RT; t += 256) {
+      const int kk = t / RT, jj = t % RT;
+      C v = cmake<C>(0, 0);
+      if (k0 + kk < nvec && j0 + jj < nvec) {
+        const double2 q = Q[(size_t)(k0 + kk) * nvec + j0 + jj];
+        v = cmake<C>(q.x, q.y);
+      }
+      qs[kk][jj] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KT; ++kk) {
+      C xv[4], qv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xv[a] = xs[ty + 16 * a][kk];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) qv[b] = qs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          acc[a][b].x += xv[a].x * qv[b].x - xv[a].y * qv[b].y;
+          acc[a][b].y += xv[a].x * qv[b].y + xv[a].y * qv[b].x;
+        }
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 4; ++a) {
+    const long long r = r0 + ty + 16 * a;
+    if (r >= rows) continue;
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx + 16 * b;
+      if (j < nvec) Out[r * ldx + j] = acc[a][b];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_copy_block(const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Out,
+                             long long rows, int nvec, int ldx) {
+  const long long n = rows * (long long)nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nvec;
+    const int v = (int)(i - r * nvec);
+    Out[r * ldx + v] = X[r * ldx + v];
+  }
+}
+
+// ---- FP64 vector helpers (Lanczos) -------------------------------------------
+// out += sum_I md[I] sum_s conj(a[I][s]) b[I][s]   (n = M spinors)
+__global__ void k_mdot(const double2* __restrict__ a, const double2* __restrict__ b,
+                       const double* __restrict__ md, long long n, double2* out) {
+  __shared__ double2 red[256];
+  double2 acc = make_double2(0, 0);
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < n;
+       I += (long long)gridDim.x * blockDim.x) {
+    const double w = md[I];
+    for (int s = 0; s < 2; ++s) {
+      const double2 x = a[2 * I + s], y = b[2 * I + s];
+      acc.x += w * (x.x * y.x + x.y * y.y);
+      acc.y += w * (x.x * y.y - x.y * y.x);
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[threadIdx.x].x += red[threadIdx.x + s].x;
+      red[threadIdx.x].y += red[threadIdx.x + s].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&out->x, red[0].x);
+    atomicAdd(&out->y, red[0].y);
+  }
+}
+
+// y -= (alpha_scale * alpha) x   (alpha read on the device)
+__global__ void k_axpy_c(double2* y, const double2* __restrict__ x, const double2* alpha,
+                         double alpha_scale, long long n) {
+  const double2 al = make_double2(alpha->x * alpha_scale, alpha->y * alpha_scale);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    y[i].x -= al.x * v.x - al.y * v.y;
+    y[i].y -= al.x * v.y + al.y * v.x;
+  }
+}
+
+__global__ void k_scale_c(double2* y, const double2* __restrict__ x, double scale, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    y[i] = make_double2(x[i].x * scale, x[i].y * scale);
+  }
+}
+
+__global__ void k_divmass(double2* y, const double* __restrict__ invmd, long long M) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 2 * M;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double w = invmd[i >> 1];
+    y[i].x *= w;
+    y[i].y *= w;
+  }
+}
+
+inline unsigned grid_for(long long n, int threads = 256) {
+  long long g = (n + threads - 1) / threads;
+  if (g > 152LL * 64) g = 152LL * 64;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_cheb_step(const cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev,
+                             cplx<T>* Xout, const T* invmd, long long M, int nvec, int ldx,
+                             double a, double cshift, double b, cudaStream_t s) {
+  const long long rows = 2 * M;
+  k_cheb_step<T><<<grid_for(rows * nvec), 256, 0, s>>>(const_cast<cplx<T>*>(Y), Xcur, Xprev, Xout,
+                                                       invmd, rows, nvec, ldx, (T)a, (T)cshift,
+                                                       (T)b);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gram(const cplx<T>* X, const cplx<T>* Y, const double* md, long long M,
+                        int nvec, int ldx, double2* S, cudaStream_t s) {
+  const long long rows = 2 * M;
+  cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double2) * (size_t)nvec * nvec, s);
+  if (e != cudaSuccess) return e;
+  const int ntile = (nvec + GT - 1) / GT;
+  const long long tiles = (long long)ntile * ntile;
+  // enough row chunks to fill the GPU a few times over
+  long long nchunk = (152LL * 8 + tiles - 1) / tiles;
+  long long per = (rows + nchunk - 1) / nchunk;
+  per = ((per + GT - 1) / GT) * GT;
+  if (per < GT) per = GT;
+  nchunk = (rows + per - 1) / per;
+  dim3 grid((unsigned)tiles, (unsigned)nchunk);
+  k_gram<T><<<grid, 256, 0, s>>>(X, Y, md, rows, nvec, ldx, per, S);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rotate(const cplx<T>* X, const double2* Q, cplx<T>* Out, long long M, int nvec,
+                          int ldx, cudaStream_t s) {
+  const long long rows = 2 * M;
+  const long long nb = ((rows + RT - 1) / RT) * ((nvec + RT - 1) / RT);
+  k_rotate<T><<<(unsigned)nb, 256, 0, s>>>(X, Q, Out, rows, nvec, ldx);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_copy_block(const cplx<T>* X, cplx<T>* Out, long long M, int nvec, int ldx,
+                              cudaStream_t s) {
+  const long long rows = 2 * M;
+  k_copy_block<T><<<grid_for(rows * nvec), 256, 0, s>>>(X, Out, rows, nvec, ldx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mdot(const double2* a, const double2* b, const double* md, long long n,
+                        double2* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double2), s);
+  if (e != cudaSuccess) return e;
+  k_mdot<<<grid_for(n), 256, 0, s>>>(a, b, md, n, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_axpy_c(double2* y, const double2* x, const double2* alpha_dev,
+                          double alpha_scale, long long n, cudaStream_t s) {
+  k_axpy_c<<<grid_for(n), 256, 0, s>>>(y, x, alpha_dev, alpha_scale, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_c(double2* y, const double2* x, double scale, long long n,
+                           cudaStream_t s) {
+  k_scale_c<<<grid_for(n), 256, 0, s>>>(y, x, scale, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_divmass(double2* y, const double* invmd, long long M, cudaStream_t s) {
+  k_divmass<<<grid_for(2 * M), 256, 0, s>>>(y, invmd, M);
+  return cudaGetLastError();
+}
+
+#define INST(T)                                                                                 \
+  template cudaError_t launch_cheb_step<T>(const cplx<T>*, const cplx<T>*, const cplx<T>*,      \
+                                           cplx<T>*, const T*, long long, int, int, double,     \
+                                           double, double, cudaStream_t);                        \
+  template cudaError_t launch_gram<T>(const cplx<T>*, const cplx<T>*, const double*, long long, \
+                                      int, int, double2*, cudaStream_t);                        \
+  template cudaError_t launch_rotate<T>(const cplx<T>*, const double2*, cplx<T>*, long long,    \
+                                        int, int, cudaStream_t);                                 \
+  template cudaError_t launch_copy_block<T>(const cplx<T>*, cplx<T>*, long long, int, int,      \
+                                            cudaStream_t);
+INST(float)
+INST(double)

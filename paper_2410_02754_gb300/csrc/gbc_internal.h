@@ -1,0 +1,221 @@
+// Internal declarations shared by the translation units of libgbchfsi.
+// Not part of the public ABI (see include/gbchfsi.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gbchfsi.h"
+
+#define GBC_MAX_P 7
+#define GBC_MAX_NPJ 32
+
+// ---------------------------------------------------------------------------
+// complex helpers (float2 / double2 carry (re, im))
+// ---------------------------------------------------------------------------
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_t<T>::type;
+
+template <typename C> __host__ __device__ inline C cmake(double re, double im) {
+  C c; c.x = re; c.y = im; return c;
+}
+
+// ---------------------------------------------------------------------------
+// mesh description passed by value to kernels
+// ---------------------------------------------------------------------------
+struct MeshDev {
+  int ncell[3];      // cells per direction
+  int nfree[3];      // free nodes per direction
+  int period[3];     // nodes per direction before periodic wrap (= ncell*p)
+  int periodic[3];
+  int p;
+  int E;
+  long long M;
+};
+
+// global free node index of local node (ix,iy,iz) of cell (cx,cy,cz), -1 on a
+// Dirichlet face
+__device__ __forceinline__ long long gbc_node(const MeshDev& m, int cx, int cy, int cz, int ix,
+                                              int iy, int iz) {
+  int g[3] = {cx * m.p + ix, cy * m.p + iy, cz * m.p + iz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (m.periodic[d]) {
+      if (g[d] >= m.period[d]) g[d] -= m.period[d];
+    } else {
+      if (g[d] == 0 || g[d] == m.period[d]) return -1;
+      g[d] -= 1;
+    }
+  }
+  return ((long long)g[2] * m.nfree[1] + g[1]) * m.nfree[0] + g[0];
+}
+
+// ---------------------------------------------------------------------------
+// per-(p, precision) 1-D operator tables, passed by value (constant bank)
+// ---------------------------------------------------------------------------
+template <typename T, int NP, int NQ> struct Tables1D {
+  T B[3][NP][NP];    // 1-D Gauss mass, physical (h_d/2 * B^)
+  T Gr[3][NP][NP];   // real part of the 1-D kinetic/k operator: 1/2 A_d
+  T Gi[3][NP][NP];   // imaginary part: -1/2 k_d (C^ - C^T)
+  T N[NP][NQ];       // l_i(xi_q) (reference; w_q J lives in the fields)
+};
+
+// host-side FP64 copy of the same tables for any p
+struct HostTables {
+  int p = 0, nq = 0;
+  std::vector<double> gll_x, gll_w, gq_x, gq_w;
+  std::vector<double> N1, D1;                  // [np][nq] values / d/dxi at Gauss points
+  std::vector<double> Bh, Ah, Ch;              // [np][np] reference 1-D mass, stiffness, advection
+};
+
+// ---------------------------------------------------------------------------
+// the context
+// ---------------------------------------------------------------------------
+struct ProjDev {
+  int natoms = 0;
+  int max_npj = 0;
+  long long nnodes_total = 0;        // sum over atoms of support-node counts
+  long long nentries = 0;
+  // host copies of small per-atom metadata
+  std::vector<int> npj, node_off, node_cnt, pv_off, delta_off, c_off;
+  // device
+  long long* d_nodes = nullptr;      // [nnodes_total] free node index per atom-support node
+  int* d_atom_npj = nullptr;         // [natoms]
+  int* d_atom_node_off = nullptr;    // [natoms]
+  int* d_atom_pv_off = nullptr;      // [natoms]
+  int* d_atom_delta_off = nullptr;   // [natoms]
+  int* d_atom_c_off = nullptr;       // [natoms] offset (in units of 2*npj rows) into C
+  double2* d_P64 = nullptr;          // [sum nodes*npj]
+  float2* d_P32 = nullptr;
+  double2* d_delta64 = nullptr;      // [sum (2npj)^2]
+  float2* d_delta32 = nullptr;
+  // chunk table for the projection kernel: (atom, first node, count)
+  int nchunks = 0;
+  int4* d_chunks = nullptr;
+  // node-centric expansion: unique support nodes and their (atom, position) incidences
+  long long nuniq = 0;
+  long long* d_uniq_node = nullptr;  // [nuniq]
+  int* d_uniq_ptr = nullptr;         // [nuniq+1]
+  int2* d_uniq_inc = nullptr;        // [nnodes_total] (atom, position in atom list)
+  // raw inputs kept on device for recomputation at a new k
+  double* d_pvals = nullptr;
+  int* d_entry_cell = nullptr;
+  int* d_entry_img = nullptr;        // [nentries*3]
+  int* d_entry_atom = nullptr;
+  long long* d_entry_pos = nullptr;  // [nentries * np^3] position in P table or -1
+  int rows_total = 0;                // sum 2*npj
+};
+
+struct gbc_ctx {
+  int dev = 0;
+  std::string err;
+  bool mesh_set = false, fields_set = false;
+  bool fields_dirty = true, proj_dirty = true;
+  gbc_precision prec = GBC_FP64;
+  MeshDev mesh{};
+  double h[3] = {1, 1, 1};
+  int nq = 0;
+  double k[3] = {0, 0, 0};
+  HostTables tab;
+  // device arrays
+  double* d_md = nullptr;            // [M]
+  double* d_invmd = nullptr;         // [M]
+  float* d_invmd32 = nullptr;
+  double* d_rawfields = nullptr;     // [4][E][nq^3] user fields (V, bx, by, bz)
+  double* d_fields64 = nullptr;      // [E][4][nq^3] w_q J (V + |k|^2/2), w_q J B_d
+  float* d_fields32 = nullptr;
+  ProjDev proj;
+  // workspaces
+  void* work[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t work_bytes[4] = {0, 0, 0, 0};
+  void* d_small = nullptr;           // small dense scratch (Gram, eigensolver)
+  size_t small_bytes = 0;
+  int* d_flag = nullptr;
+  // optional per-kernel-family timing (gbc_set_timing)
+  bool timing = false;
+  struct TimedLaunch { int family; cudaEvent_t a, b; };
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+// kernel families reported by gbc_get_timing
+enum { FAM_HX_LOCAL = 0, FAM_NONLOCAL = 1, FAM_CHEB = 2, FAM_GRAM = 3, FAM_ROTATE = 4,
+       FAM_DENSE = 5, FAM_COUNT = 6 };
+// brackets launches with CUDA events on stream s when timing is enabled
+struct TimerScope {
+  gbc_ctx* c; int fam; cudaStream_t s; cudaEvent_t a = nullptr, b = nullptr;
+  TimerScope(gbc_ctx* c_, int fam_, cudaStream_t s_);
+  ~TimerScope();
+};
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+gbc_status gbc_fail(gbc_ctx* c, gbc_status s, const std::string& msg);
+gbc_status gbc_cuda_fail(gbc_ctx* c, cudaError_t e, const char* where);
+#define GBC_CU(ctx, call)                                              \
+  do {                                                                 \
+    cudaError_t _e = (call);                                           \
+    if (_e != cudaSuccess) return gbc_cuda_fail((ctx), _e, #call);     \
+  } while (0)
+#define GBC_TRY(call)                     \
+  do {                                    \
+    gbc_status _s = (call);               \
+    if (_s != GBC_OK) return _s;          \
+  } while (0)
+
+gbc_status gbc_ensure_work(gbc_ctx* c, int slot, size_t bytes);
+gbc_status gbc_ensure_small(gbc_ctx* c, size_t bytes);
+gbc_status gbc_prepare(gbc_ctx* c);    // (re)builds fields / projector tables if dirty
+
+// ---------------------------------------------------------------------------
+// launchers implemented in the .cu files
+// ---------------------------------------------------------------------------
+// hx_local_*.cu : Y += H^loc X (cell-level apply + atomic assembly)
+cudaError_t launch_hx_local_f64(const gbc_ctx* c, const double2* X, double2* Y, int nvec, int ldx,
+                                cudaStream_t s);
+cudaError_t launch_hx_local_f32(const gbc_ctx* c, const float2* X, float2* Y, int nvec, int ldx,
+                                cudaStream_t s);
+// nonlocal.cu : Y += sum_a P Delta P^H X
+template <typename T>
+cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx,
+                            cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s);
+// setup.cu
+gbc_status setup_tables(gbc_ctx* c);
+gbc_status setup_fields(gbc_ctx* c);
+gbc_status setup_projectors(gbc_ctx* c);
+gbc_status setup_mass(gbc_ctx* c);
+gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, const int* nsupp,
+                                     const int* supp_cell, const int* supp_img,
+                                     const double* pvals, const double* delta);
+void free_projectors(ProjDev& pj);
+// blas.cu : block kernels
+template <typename T>
+cudaError_t launch_cheb_step(const cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev,
+                             cplx<T>* Xout, const T* invmd, long long M, int nvec, int ldx,
+                             double a, double cshift, double b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gram(const cplx<T>* X, const cplx<T>* Y, const double* md, long long M,
+                        int nvec, int ldx, double2* S, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rotate(const cplx<T>* X, const double2* Q, cplx<T>* Out, long long M, int nvec,
+                          int ldx, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_block(const cplx<T>* X, cplx<T>* Out, long long M, int nvec, int ldx,
+                              cudaStream_t s);
+// dense.cu : small dense FP64 linear algebra on the device
+gbc_status dense_cholesky_inv_h(gbc_ctx* c, double2* S, int n, double2* Q, cudaStream_t s);
+gbc_status dense_eigh(gbc_ctx* c, double2* A, int n, double* evals_dev, double2* Q,
+                      cudaStream_t s);
+cudaError_t launch_hermitize(double2* A, int n, cudaStream_t s);
+// lanczos helpers
+cudaError_t launch_mdot(const double2* a, const double2* b, const double* md, long long n,
+                        double2* out, cudaStream_t s);
+cudaError_t launch_axpy_c(double2* y, const double2* x, const double2* alpha_dev, double alpha_scale,
+                          long long n, cudaStream_t s);
+cudaError_t launch_scale_c(double2* y, const double2* x, double scale, long long n, cudaStream_t s);
+cudaError_t launch_divmass(double2* y, const double* invmd, long long M, cudaStream_t s);

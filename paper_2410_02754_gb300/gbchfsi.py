@@ -1,0 +1,238 @@
+"""ctypes binding of libgbchfsi (the C ABI in include/gbchfsi.h).
+
+Argument marshalling only: every arithmetic step runs in the library's CUDA
+kernels.  Device blocks are torch CUDA tensors used as plain memory:
+complex128 for ``FP64``, complex64 for ``FP32``, shape [M, 2, ldx] (or a
+contiguous view with that layout).  The library is loaded from this package
+directory; importing this module on a machine without the built library or
+without a CUDA device raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbchfsi.so")
+
+FP64, FP32 = 0, 1
+STATUS = {0: "GBC_OK", 1: "GBC_EINVAL", 2: "GBC_ENOMEM", 3: "GBC_ECUDA", 4: "GBC_ESTATE",
+          5: "GBC_ENOTPD", 6: "GBC_ETIMEOUT", 7: "GBC_EUNSUPPORTED"}
+
+# every entry point declared in include/gbchfsi.h
+EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_set_mesh",
+           "gbc_set_kpoint", "gbc_set_fields", "gbc_set_projectors", "gbc_set_precision",
+           "gbc_get_nnodes", "gbc_get_mass", "gbc_apply_h", "gbc_lanczos_bounds", "gbc_filter",
+           "gbc_cholgs", "gbc_rayleigh_ritz", "gbc_set_timing", "gbc_get_timing"]
+FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
+
+
+class GbcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load (once) and type the shared library.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libgbchfsi.so not built at {path}; run __graft_entry__.build()")
+    lib = ct.CDLL(path)
+    P, I, D, V = ct.c_void_p, ct.c_int, ct.c_double, ct.c_void_p
+    IP, DP = ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)
+    sig = {
+        "gbc_create": ([ct.POINTER(P), I], I),
+        "gbc_destroy": ([P], None),
+        "gbc_last_error": ([P], ct.c_char_p),
+        "gbc_version": ([], ct.c_char_p),
+        "gbc_set_mesh": ([P, IP, DP, I, I, IP], I),
+        "gbc_set_kpoint": ([P, DP], I),
+        "gbc_set_fields": ([P, DP, DP, DP, DP], I),
+        "gbc_set_projectors": ([P, I, IP, IP, IP, IP, DP, DP], I),
+        "gbc_set_precision": ([P, I], I),
+        "gbc_get_nnodes": ([P, ct.POINTER(ct.c_longlong)], I),
+        "gbc_get_mass": ([P, DP], I),
+        "gbc_apply_h": ([P, V, V, I, I, V], I),
+        "gbc_lanczos_bounds": ([P, V, I, DP, DP, V], I),
+        "gbc_filter": ([P, V, I, I, I, D, D, D, V], I),
+        "gbc_cholgs": ([P, V, I, I, V], I),
+        "gbc_rayleigh_ritz": ([P, V, I, I, DP, V], I),
+        "gbc_set_timing": ([P, I], I),
+        "gbc_get_timing": ([P, I, DP, ct.POINTER(ct.c_longlong)], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _iarr(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ct.POINTER(ct.c_int))
+
+
+def _darr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ct.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+class Context:
+    """One problem (mesh, k-point, fields, projectors) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        h = ct.c_void_p()
+        st = self.lib.gbc_create(ct.byref(h), device)
+        if st != 0:
+            raise GbcError(st, f"gbc_create(device={device}) failed")
+        self.h = h
+        self.device = device
+        self.prec = FP64
+        self.nnodes = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gbc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        if st != 0:
+            raise GbcError(st, self.lib.gbc_last_error(self.h).decode())
+
+    # ---- problem definition ---------------------------------------------------
+    def set_mesh(self, ncell, h, p, nq, periodic):
+        nc, ncp = _iarr(ncell)
+        hh, hp = _darr(h)
+        pe, pp = _iarr([1 if b else 0 for b in periodic])
+        self._chk(self.lib.gbc_set_mesh(self.h, ncp, hp, int(p), int(nq), pp))
+        n = ct.c_longlong()
+        self._chk(self.lib.gbc_get_nnodes(self.h, ct.byref(n)))
+        self.nnodes = n.value
+
+    def set_kpoint(self, k):
+        kk, kp = _darr(k)
+        self._chk(self.lib.gbc_set_kpoint(self.h, kp))
+
+    def set_fields(self, veff, bx, by, bz):
+        arrs = [_darr(x) for x in (veff, bx, by, bz)]
+        self._chk(self.lib.gbc_set_fields(self.h, *[p for _, p in arrs]))
+
+    def set_projectors(self, natoms, npj, nsupp, supp_cell, supp_img, pvals, delta):
+        if natoms == 0:
+            self._chk(self.lib.gbc_set_projectors(self.h, 0, None, None, None, None, None, None))
+            return
+        a1, p1 = _iarr(npj)
+        a2, p2 = _iarr(nsupp)
+        a3, p3 = _iarr(supp_cell)
+        a4, p4 = _iarr(supp_img)
+        a5, p5 = _darr(pvals)
+        d = np.ascontiguousarray(delta, dtype=np.complex128)
+        a6, p6 = _darr(d.view(np.float64))
+        self._chk(self.lib.gbc_set_projectors(self.h, int(natoms), p1, p2, p3, p4, p5, p6))
+
+    def set_problem(self, prob):
+        """Load a problem object with attributes ncell, h, p, nq, periodic, k,
+        veff, bx, by, bz and flat_projectors() (the synthetic generator's)."""
+        self.set_mesh(prob.ncell, prob.h, prob.p, prob.nq, prob.periodic)
+        self.set_kpoint(prob.k)
+        self.set_fields(prob.veff, prob.bx, prob.by, prob.bz)
+        fp = prob.flat_projectors()
+        self.set_projectors(fp["natoms"], fp["npj"], fp["nsupp"], fp["supp_cell"], fp["supp_img"],
+                            fp["pvals"], fp["delta"])
+
+    def set_precision(self, prec):
+        self._chk(self.lib.gbc_set_precision(self.h, int(prec)))
+        self.prec = prec
+
+    def mass(self):
+        md = np.empty(self.nnodes, np.float64)
+        self._chk(self.lib.gbc_get_mass(self.h, md.ctypes.data_as(ct.POINTER(ct.c_double))))
+        return md
+
+    # ---- block calls ------------------------------------------------------------
+    def _block(self, X):
+        import torch
+        want = torch.complex128 if self.prec == FP64 else torch.complex64
+        if not X.is_cuda:
+            raise ValueError("block must be a CUDA tensor")
+        if X.dtype != want:
+            raise ValueError(f"block dtype {X.dtype} does not match the precision ({want})")
+        if X.dim() != 3 or X.shape[0] != self.nnodes or X.shape[1] != 2:
+            raise ValueError(f"block must have shape [M={self.nnodes}, 2, ldx]")
+        if X.stride(2) != 1 or X.stride(1) != X.shape[2] or X.stride(0) != 2 * X.shape[2]:
+            raise ValueError("block must be contiguous [M][2][ldx]")
+        return ct.c_void_p(X.data_ptr()), X.shape[2]
+
+    def apply_h(self, X, Y, nvec=None, stream=None):
+        px, ldx = self._block(X)
+        py, ldy = self._block(Y)
+        if ldx != ldy:
+            raise ValueError("X and Y need the same ldx")
+        nvec = ldx if nvec is None else nvec
+        self._chk(self.lib.gbc_apply_h(self.h, px, py, int(nvec), int(ldx), _stream_ptr(stream)))
+
+    def filter(self, X, degree, lT, lmax, lmin, nvec=None, stream=None):
+        px, ldx = self._block(X)
+        nvec = ldx if nvec is None else nvec
+        self._chk(self.lib.gbc_filter(self.h, px, int(nvec), int(ldx), int(degree), float(lT),
+                                      float(lmax), float(lmin), _stream_ptr(stream)))
+
+    def cholgs(self, X, nvec=None, stream=None):
+        px, ldx = self._block(X)
+        nvec = ldx if nvec is None else nvec
+        self._chk(self.lib.gbc_cholgs(self.h, px, int(nvec), int(ldx), _stream_ptr(stream)))
+
+    def rayleigh_ritz(self, X, nvec=None, stream=None):
+        px, ldx = self._block(X)
+        nvec = ldx if nvec is None else nvec
+        out = np.empty(nvec, np.float64)
+        self._chk(self.lib.gbc_rayleigh_ritz(self.h, px, int(nvec), int(ldx),
+                                             out.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                             _stream_ptr(stream)))
+        return out
+
+    def lanczos_bounds(self, v0, steps, stream=None):
+        import torch
+        if not (v0.is_cuda and v0.dtype == torch.complex128 and v0.is_contiguous()
+                and tuple(v0.shape) == (self.nnodes, 2)):
+            raise ValueError("v0 must be a contiguous complex128 CUDA tensor [M, 2]")
+        lo, hi = ct.c_double(), ct.c_double()
+        self._chk(self.lib.gbc_lanczos_bounds(self.h, ct.c_void_p(v0.data_ptr()), int(steps),
+                                              ct.byref(lo), ct.byref(hi), _stream_ptr(stream)))
+        return lo.value, hi.value
+
+    # ---- tracing --------------------------------------------------------------------
+    def set_timing(self, enable=True):
+        self._chk(self.lib.gbc_set_timing(self.h, 1 if enable else 0))
+
+    def timing(self):
+        """{family: (total_ms, launches)} since the last set_timing."""
+        out = {}
+        for name, fam in FAMILIES.items():
+            t, n = ct.c_double(), ct.c_longlong()
+            self._chk(self.lib.gbc_get_timing(self.h, fam, ct.byref(t), ct.byref(n)))
+            out[name] = (t.value, n.value)
+        return out

@@ -1,0 +1,209 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: H.X relative Frobenius 1e-12 (FP64) / 1e-5 (FP32); filter outputs
+1e-11 / 1e-5; Ritz values 1e-6 Ha for every path (they meet far tighter).
+"""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import chfsi as oc
+from oracle import fe
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def g():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2410_02754_gb300 as pkg
+    return pkg
+
+
+def make_ctx(g, prob, prec):
+    ctx = g.Context(0)
+    ctx.set_problem(prob)
+    ctx.set_precision(prec)
+    return ctx
+
+
+def to_dev(X, prec, ldx=None):
+    nv = X.shape[2]
+    ldx = ldx or nv
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    out = torch.zeros((X.shape[0], 2, ldx), dtype=dt, device="cuda")
+    out[:, :, :nv] = torch.from_numpy(X).to(dt).cuda()
+    return out
+
+
+CASES = [
+    # ncell, p, periodic, k, natoms, nvec, ldx
+    ((2, 2, 2), 2, (1, 1, 1), (0, 0, 0), 1, 3, 3),
+    ((3, 2, 2), 3, (1, 1, 0), (0.1, -0.2, 0.3), 2, 5, 7),
+    ((2, 3, 2), 4, (1, 1, 1), (0.2, 0.1, -0.1), 2, 9, 9),
+    ((2, 2, 3), 5, (0, 1, 1), (0.0, 0.3, 0.0), 1, 4, 4),
+    ((2, 2, 2), 6, (1, 1, 1), (0.05, 0.05, 0.05), 2, 6, 8),
+    ((2, 2, 2), 7, (1, 0, 1), (0.1, 0.0, 0.2), 1, 2, 2),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"p{c[1]}-{c[0]}-per{c[2]}")
+def test_apply_h_fp64_and_fp32(g, case):
+    ncell, p, per, k, natoms, nvec, ldx = case
+    prob = syn.make_problem(ncell=ncell, h=(1.1, 1.2, 1.3), p=p, periodic=per, k=k,
+                            natoms=natoms, rc=1.2, seed=p, channels=((0.5, 0), (0.5, 1)))
+    d = fe.Discretisation(prob)
+    X = syn.random_block(d.mesh.nnodes, nvec, 11)
+    ref = d.apply_h(X)
+    for prec, tol in ((0, 1e-12), (1, 1e-5)):
+        ctx = make_ctx(g, prob, prec)
+        Xd = to_dev(X, prec, ldx)
+        Yd = torch.full_like(Xd, 7.0)
+        ctx.apply_h(Xd, Yd, nvec=nvec)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().numpy()
+        assert rel(Y[:, :, :nvec], ref) < tol, (prec, rel(Y[:, :, :nvec], ref))
+        ctx.close()
+
+
+def test_apply_h_empty_block_and_no_atoms(g):
+    prob = syn.make_problem(ncell=(2, 2, 2), h=(1, 1, 1), p=3, natoms=0, seed=1)
+    d = fe.Discretisation(prob)
+    ctx = make_ctx(g, prob, 0)
+    Xd = to_dev(syn.random_block(d.mesh.nnodes, 2, 1), 0)
+    Yd = torch.ones_like(Xd)
+    ctx.apply_h(Xd, Yd, nvec=0)                        # empty block: Y zeroed, nothing else
+    torch.cuda.synchronize()
+    assert float(Yd.abs().max()) == 0.0
+    ref = d.apply_h(Xd.cpu().numpy())
+    ctx.apply_h(Xd, Yd)
+    torch.cuda.synchronize()
+    assert rel(Yd.cpu().numpy(), ref) < 1e-12
+
+
+def test_errors_are_reported(g):
+    prob = syn.make_problem(ncell=(2, 2, 2), h=(1, 1, 1), p=3, natoms=1, seed=1)
+    ctx = g.Context(0)
+    with pytest.raises(g.GbcError):
+        ctx.set_mesh((2, 2, 2), (1, 1, 1), 3, 4, (1, 1, 1))     # nq != p + 2
+    with pytest.raises(g.GbcError):
+        ctx.set_mesh((2, 2, 2), (1, 1, 1), 9, 11, (1, 1, 1))    # p out of range
+    ctx.set_problem(prob)
+    X = to_dev(syn.random_block(ctx.nnodes, 4, 1), 0)
+    with pytest.raises(g.GbcError):
+        ctx.filter(X, 5, 3.0, 2.0, 1.0)                          # lmin < lT < lmax violated
+    Z = torch.zeros_like(X)
+    with pytest.raises(g.GbcError) as ei:
+        ctx.cholgs(Z)                                            # S = 0 is not positive definite
+    assert ei.value.status == 5
+    assert float(Z.abs().max()) == 0.0                          # X left unchanged
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
+def test_filter_matches_oracle(g, prec, tol):
+    prob = syn.make_problem(ncell=(3, 2, 2), h=(1.1, 1.1, 1.1), p=4, k=(0.1, 0.2, -0.1),
+                            natoms=2, rc=1.2, seed=3)
+    d = fe.Discretisation(prob)
+    X = syn.random_block(d.mesh.nnodes, 6, 4)
+    lT, lmax, lmin = 1.5, 90.0, -2.5
+    for m in (1, 2, 7):
+        ref = oc.cheb_filter(d.apply_htilde, X, m, lT, lmax, lmin)
+        ctx = make_ctx(g, prob, prec)
+        Xd = to_dev(X, prec)
+        ctx.filter(Xd, m, lT, lmax, lmin)
+        torch.cuda.synchronize()
+        assert rel(Xd.cpu().numpy(), ref) < tol, (m, rel(Xd.cpu().numpy(), ref))
+        ctx.close()
+
+
+def test_lanczos_bounds_match_oracle(g):
+    prob = syn.make_problem(ncell=(2, 2, 3), h=(1.2, 1.2, 1.2), p=3, k=(0.1, 0, 0), natoms=2,
+                            rc=1.2, seed=4)
+    d = fe.Discretisation(prob)
+    v0 = syn.random_start(d.mesh.nnodes, 3)
+    lo, hi = oc.lanczos_bounds(d.apply_htilde, d.md, v0, 10)
+    ctx = make_ctx(g, prob, 0)
+    glo, ghi = ctx.lanczos_bounds(torch.from_numpy(v0).cuda(), 10)
+    assert abs(glo - lo) < 1e-9 * abs(hi) and abs(ghi - hi) < 1e-9 * abs(hi)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cholgs_and_rayleigh_ritz(g, prec):
+    prob = syn.make_problem(ncell=(2, 2, 2), h=(1.2, 1.2, 1.2), p=4, k=(0.1, 0.0, 0.2),
+                            natoms=2, rc=1.2, seed=6)
+    d = fe.Discretisation(prob)
+    X = syn.random_block(d.mesh.nnodes, 12, 2)
+    ctx = make_ctx(g, prob, prec)
+    Xd = to_dev(X, prec)
+    ctx.cholgs(Xd)
+    Q = Xd.cpu().numpy().astype(np.complex128)
+    S = oc.gram(Q, d.md)
+    assert np.abs(S - np.eye(12)).max() < (1e-12 if prec == 0 else 2e-5)
+    if prec == 0:
+        assert rel(Q, oc.cholgs(X, d.md)) < 1e-10
+    ritz = ctx.rayleigh_ritz(Xd)
+    ref, Xr, _ = oc.rayleigh_ritz(d.apply_h, oc.cholgs(X, d.md))
+    assert np.abs(ritz - ref).max() < (1e-10 if prec == 0 else 1e-4)
+    # Ritz vectors: compare the spanned subspaces via M_D-projectors on a random probe
+    Xg = Xd.cpu().numpy().astype(np.complex128)
+    Z = syn.random_block(d.mesh.nnodes, 3, 9)
+    Pg = Xg.reshape(-1, 12) @ oc.gram(Xg, d.md, Z)
+    Pr = Xr.reshape(-1, 12) @ oc.gram(Xr, d.md, Z)
+    assert rel(Pg, Pr) < (1e-9 if prec == 0 else 1e-4)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_c0_chfsi_ritz_values(g, prec):
+    """Config-0 workload end to end: Lanczos bounds, cycle 0, 3 x (filter, CholGS, RR)."""
+    prob = syn.config("c0")
+    c = syn.CONFIGS["c0"]
+    d = fe.Discretisation(prob)
+    M = d.mesh.nnodes
+    X0 = syn.random_block(M, c["nvec"], 0)
+    v0 = syn.random_start(M, 0)
+    lmin, lmax = oc.lanczos_bounds(d.apply_htilde, d.md, v0, c["lanczos"])
+    hist, _ = oc.chfsi(d.apply_h, d.md, X0, c["cycles"], c["degree"], lmin, lmax)
+    ctx = make_ctx(g, prob, prec)
+    glo, ghi = ctx.lanczos_bounds(torch.from_numpy(v0).cuda(), c["lanczos"])
+    assert abs(ghi - lmax) < 1e-8 * abs(lmax)
+    Xd = to_dev(X0, prec)
+    ctx.cholgs(Xd)
+    ritz = ctx.rayleigh_ritz(Xd)
+    for cyc in range(c["cycles"]):
+        ctx.filter(Xd, c["degree"], float(ritz[-1]), lmax, lmin)
+        ctx.cholgs(Xd)
+        ritz = ctx.rayleigh_ritz(Xd)
+    nconv = c["nvec"] // 2
+    err = np.abs(ritz - hist[-1])
+    assert err[:nconv].max() < 1e-6, err
+    ctx.close()
+
+
+def test_c1_full_size_sampled_rows(g):
+    """Config-1 mesh and atoms at full size (884,736 nodes, 64 atoms, 18 projectors,
+    k != 0), FP64 and FP32 H.X checked on sampled rows against the oracle."""
+    prob = syn.config("c1", kindex=1)
+    d = fe.Discretisation(prob)
+    M = d.mesh.nnodes
+    rng = np.random.default_rng(0)
+    rows = np.unique(rng.integers(0, M, 40))
+    X = syn.random_block(M, 4, 3)
+    ref = d.apply_h_rows(X, rows)
+    for prec, tol in ((0, 1e-12), (1, 1e-5)):
+        ctx = make_ctx(g, prob, prec)
+        Xd = to_dev(X, prec)
+        Yd = torch.empty_like(Xd)
+        ctx.apply_h(Xd, Yd)
+        torch.cuda.synchronize()
+        got = Yd[torch.from_numpy(rows).cuda()].cpu().numpy()
+        assert rel(got, ref) < tol, (prec, rel(got, ref))
+        ctx.close()
