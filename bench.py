@@ -194,7 +194,7 @@ def run_gpu(args):
         X = torch.from_numpy(X0).to(torch.complex64).cuda()
         c.cholgs(X)
         ritz = c.rayleigh_ritz(X)
-        bounds.append((float(ritz[-1]), hi, lo))
+        bounds.append((float(ritz[-1]), hi, min(lo, float(ritz[0]))))
         X32.append(X)
     torch.cuda.synchronize()
 
@@ -300,6 +300,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        lo = min(lo, float(r0[0]))
         c64.filter(Xa, degree, lT, hi, lo)
         e1.record(stream)
         torch.cuda.synchronize()

@@ -226,6 +226,9 @@ def lanczos_bounds(apply_htilde, md, v0, steps: int):
 def chfsi(apply_h, md, X0, cycles: int, degree: int, lmin: float, lmax: float):
     """Cycle 0 = CholGS + RR on X0 (sets lambda_T = max Ritz value); then
     ``cycles`` x (filter -> CholGS -> RR), lambda_T updated after each RR.
+    The filter is normalised at min(lmin, lowest Ritz value of the previous RR):
+    a few Lanczos steps do not bound the spectrum from below, and the
+    normalisation point must lie below the damped interval [lambda_T, lmax].
     Returns (list of Ritz-value arrays, final X)."""
     def apply_ht(Z):
         return apply_h(Z) / md[:, None, None]
@@ -235,7 +238,7 @@ def chfsi(apply_h, md, X0, cycles: int, degree: int, lmin: float, lmax: float):
     history = [ritz]
     for _ in range(cycles):
         lT = float(ritz[-1])
-        X = cheb_filter(apply_ht, X, degree, lT, lmax, lmin)
+        X = cheb_filter(apply_ht, X, degree, lT, lmax, min(lmin, float(ritz[0])))
         X = cholgs(X, md)
         ritz, X, _ = rayleigh_ritz(apply_h, X)
         history.append(ritz)

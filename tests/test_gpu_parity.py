@@ -179,7 +179,7 @@ def test_c0_chfsi_ritz_values(g, prec):
     ctx.cholgs(Xd)
     ritz = ctx.rayleigh_ritz(Xd)
     for cyc in range(c["cycles"]):
-        ctx.filter(Xd, c["degree"], float(ritz[-1]), lmax, lmin)
+        ctx.filter(Xd, c["degree"], float(ritz[-1]), lmax, min(lmin, float(ritz[0])))
         ctx.cholgs(Xd)
         ritz = ctx.rayleigh_ritz(Xd)
     nconv = c["nvec"] // 2
