@@ -175,7 +175,8 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     ge.build()
     cfg = syn.CONFIGS[args.config]
-    nvec, degree = cfg["nvec"], cfg["degree"]
+    nvec = args.nvec or cfg["nvec"]
+    degree = args.degree or cfg["degree"]
     prob = syn.config(args.config, seed=0)
     ks = syn.mp_kpoints(*cfg["kgrid"], prob.box)
     if args.kpoints:
@@ -394,6 +395,8 @@ def main():
     ap.add_argument("--impl", default="gbchfsi", choices=["gbchfsi", "reference"])
     ap.add_argument("--config", default="c1")
     ap.add_argument("--kpoints", type=int, default=0, help="use only the first K k-points")
+    ap.add_argument("--nvec", type=int, default=0, help="override the block size (profiling runs)")
+    ap.add_argument("--degree", type=int, default=0, help="override the degree (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -218,6 +218,29 @@ gbc_status rr_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, double* ritz, cudaStr
   return GBC_OK;
 }
 
+// The mixed path keeps complex64 blocks for the filter but runs CholGS and
+// Rayleigh-Ritz on an FP64 copy (FP64 H.X, FP64 Gram, FP64 rotation): an FP32
+// H.X would put a first-order error eps32 * ||H~|| into X^H H X and hence into
+// the Ritz values.  Work slot 4.. holds the FP64 copy.
+struct cholgs_tag {};
+struct rr_tag {};
+template <typename Tag>
+gbc_status promoted(gbc_ctx* c, float2* X, int nvec, int ldx, double* ritz, cudaStream_t s) {
+  const size_t bytes64 = sizeof(double2) * 2 * (size_t)c->mesh.M * nvec;
+  GBC_TRY(gbc_ensure_work(c, 4, bytes64));
+  double2* X64 = (double2*)c->work[4];
+  GBC_CU(c, launch_convert_block(X, ldx, X64, nvec, c->mesh.M, nvec, s));
+  gbc_status st;
+  if (std::is_same<Tag, cholgs_tag>::value)
+    st = cholgs_t<double>(c, X64, nvec, nvec, s);
+  else
+    st = rr_t<double>(c, X64, nvec, nvec, ritz, s);
+  if (st != GBC_OK) return st;
+  GBC_CU(c, launch_convert_block(X64, nvec, X, ldx, c->mesh.M, nvec, s));
+  GBC_CU(c, cudaStreamSynchronize(s));
+  return GBC_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -255,7 +278,7 @@ void gbc_destroy(gbc_ctx* c) {
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
   void* ptrs[] = {c->d_md, c->d_invmd, c->d_invmd32, c->d_rawfields, c->d_fields64, c->d_fields32,
-                  c->work[0], c->work[1], c->work[2], c->work[3], c->d_small, c->d_flag};
+                  c->work[0], c->work[1], c->work[2], c->work[3], c->work[4], c->d_small, c->d_flag};
   for (void* p : ptrs) cudaFree(p);
   delete c;
 }
@@ -412,7 +435,7 @@ gbc_status gbc_cholgs(gbc_ctx* c, void* X, int nvec, int ldx, void* stream) {
   GBC_TRY(gbc_prepare(c));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->prec == GBC_FP64) return cholgs_t<double>(c, (double2*)X, nvec, ldx, s);
-  return cholgs_t<float>(c, (float2*)X, nvec, ldx, s);
+  return promoted<cholgs_tag>(c, (float2*)X, nvec, ldx, nullptr, s);
 }
 
 gbc_status gbc_rayleigh_ritz(gbc_ctx* c, void* X, int nvec, int ldx, double* ritz, void* stream) {
@@ -423,7 +446,7 @@ gbc_status gbc_rayleigh_ritz(gbc_ctx* c, void* X, int nvec, int ldx, double* rit
   GBC_TRY(gbc_prepare(c));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->prec == GBC_FP64) return rr_t<double>(c, (double2*)X, nvec, ldx, ritz, s);
-  return rr_t<float>(c, (float2*)X, nvec, ldx, ritz, s);
+  return promoted<rr_tag>(c, (float2*)X, nvec, ldx, ritz, s);
 }
 
 gbc_status gbc_lanczos_bounds(gbc_ctx* c, const void* v0, int steps, double* lmin, double* lmax,

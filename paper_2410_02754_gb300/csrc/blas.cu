@@ -176,6 +176,22 @@ __global__ void k_copy_block(const cplx<T>* __restrict__ X, cplx<T>* __restrict_
   }
 }
 
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ X, int ldx, B* __restrict__ Out, int ldo,
+                          long long rows, int nvec) {
+  const long long n = rows * (long long)nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nvec;
+    const int v = (int)(i - r * nvec);
+    const A a = X[r * ldx + v];
+    B b;
+    b.x = a.x;
+    b.y = a.y;
+    Out[r * ldo + v] = b;
+  }
+}
+
 // ---- FP64 vector helpers (Lanczos) -------------------------------------------
 // out += sum_I md[I] sum_s conj(a[I][s]) b[I][s]   (n = M spinors)
 __global__ void k_mdot(const double2* __restrict__ a, const double2* __restrict__ b,
@@ -287,6 +303,17 @@ cudaError_t launch_copy_block(const cplx<T>* X, cplx<T>* Out, long long M, int n
                               cudaStream_t s) {
   const long long rows = 2 * M;
   k_copy_block<T><<<grid_for(rows * nvec), 256, 0, s>>>(X, Out, rows, nvec, ldx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_block(const float2* X, int ldx, double2* Out, int ldo, long long M,
+                                 int nvec, cudaStream_t s) {
+  k_convert<float2, double2><<<grid_for(2 * M * nvec), 256, 0, s>>>(X, ldx, Out, ldo, 2 * M, nvec);
+  return cudaGetLastError();
+}
+cudaError_t launch_convert_block(const double2* X, int ldx, float2* Out, int ldo, long long M,
+                                 int nvec, cudaStream_t s) {
+  k_convert<double2, float2><<<grid_for(2 * M * nvec), 256, 0, s>>>(X, ldx, Out, ldo, 2 * M, nvec);
   return cudaGetLastError();
 }
 

@@ -130,8 +130,8 @@ struct gbc_ctx {
   float* d_fields32 = nullptr;
   ProjDev proj;
   // workspaces
-  void* work[4] = {nullptr, nullptr, nullptr, nullptr};
-  size_t work_bytes[4] = {0, 0, 0, 0};
+  void* work[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t work_bytes[5] = {0, 0, 0, 0, 0};
   void* d_small = nullptr;           // small dense scratch (Gram, eigensolver)
   size_t small_bytes = 0;
   int* d_flag = nullptr;
@@ -204,6 +204,11 @@ cudaError_t launch_gram(const cplx<T>* X, const cplx<T>* Y, const double* md, lo
 template <typename T>
 cudaError_t launch_rotate(const cplx<T>* X, const double2* Q, cplx<T>* Out, long long M, int nvec,
                           int ldx, cudaStream_t s);
+// block precision conversion (float2 <-> double2), rows of 2M, nvec columns
+cudaError_t launch_convert_block(const float2* X, int ldx, double2* Out, int ldo, long long M,
+                                 int nvec, cudaStream_t s);
+cudaError_t launch_convert_block(const double2* X, int ldx, float2* Out, int ldo, long long M,
+                                 int nvec, cudaStream_t s);
 template <typename T>
 cudaError_t launch_copy_block(const cplx<T>* X, cplx<T>* Out, long long M, int nvec, int ldx,
                               cudaStream_t s);

@@ -100,31 +100,36 @@ __global__ void nl_couple(const cplx<T>* __restrict__ Cbuf, cplx<T>* __restrict_
 }
 
 // Y[node][s][v] += sum over atoms whose support holds node of sum_chi P[pos][chi] Cp[2chi+s][v]
+// A block owns kExpNodes consecutive unique support nodes and 128 columns.
+constexpr int kExpNodes = 16;
 template <typename T>
 __global__ void __launch_bounds__(kCols)
 nl_expand(cplx<T>* __restrict__ Y, int ldx, int nvec, const long long* __restrict__ uniq_node,
-          const int* __restrict__ uniq_ptr, const int2* __restrict__ uniq_inc,
+          const int* __restrict__ uniq_ptr, const int2* __restrict__ uniq_inc, long long nuniq,
           const cplx<T>* __restrict__ P, const int* __restrict__ atom_npj,
           const int* __restrict__ atom_pv_off, const int* __restrict__ atom_c_off,
           const cplx<T>* __restrict__ Cp) {
   using C = cplx<T>;
-  const long long u = blockIdx.x;
+  const long long u0 = (long long)blockIdx.x * kExpNodes;
+  const long long u1 = min(nuniq, u0 + kExpNodes);
   const int col = blockIdx.y * kCols + threadIdx.x;
   if (col >= 2 * nvec) return;
   const int s = col / nvec, v = col % nvec;
-  C acc = cmake<C>(0, 0);
-  for (int k = uniq_ptr[u]; k < uniq_ptr[u + 1]; ++k) {
-    const int2 inc = uniq_inc[k];
-    const int npj = atom_npj[inc.x];
-    const C* Pr = P + atom_pv_off[inc.x] + (size_t)inc.y * npj;
-    const C* Cr = Cp + (size_t)atom_c_off[inc.x] * nvec + v;
-    for (int c = 0; c < npj; ++c) cmac(acc, Pr[c], Cr[(size_t)(2 * c + s) * nvec]);
+  for (long long u = u0; u < u1; ++u) {
+    C acc = cmake<C>(0, 0);
+    for (int k = uniq_ptr[u]; k < uniq_ptr[u + 1]; ++k) {
+      const int2 inc = uniq_inc[k];
+      const int npj = atom_npj[inc.x];
+      const C* Pr = P + atom_pv_off[inc.x] + (size_t)inc.y * npj;
+      const C* Cr = Cp + (size_t)atom_c_off[inc.x] * nvec + v + (size_t)s * nvec;
+      for (int c = 0; c < npj; ++c) cmac(acc, Pr[c], Cr[(size_t)(2 * c) * nvec]);
+    }
+    C* y = &Y[(uniq_node[u] * 2 + s) * ldx + v];
+    C o = *y;
+    o.x += acc.x;
+    o.y += acc.y;
+    *y = o;
   }
-  C* y = &Y[(uniq_node[u] * 2 + s) * ldx + v];
-  C o = *y;
-  o.x += acc.x;
-  o.y += acc.y;
-  *y = o;
 }
 
 template <typename T, int MAXPJ>
@@ -163,9 +168,10 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
   if (e != cudaSuccess) return e;
   const cplx<T>* P = std::is_same<T, double>::value ? (const cplx<T>*)pj.d_P64
                                                     : (const cplx<T>*)pj.d_P32;
-  dim3 g3((unsigned)pj.nuniq, (2 * nvec + kCols - 1) / kCols);
-  nl_expand<T><<<g3, kCols, 0, s>>>(Y, ldx, nvec, pj.d_uniq_node, pj.d_uniq_ptr, pj.d_uniq_inc, P,
-                                   pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off, Cpbuf);
+  dim3 g3((unsigned)((pj.nuniq + kExpNodes - 1) / kExpNodes), (2 * nvec + kCols - 1) / kCols);
+  nl_expand<T><<<g3, kCols, 0, s>>>(Y, ldx, nvec, pj.d_uniq_node, pj.d_uniq_ptr, pj.d_uniq_inc,
+                                   pj.nuniq, P, pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off,
+                                   Cpbuf);
   return cudaGetLastError();
 }
 
