@@ -128,10 +128,28 @@ gbc_status gbc_lanczos_bounds(gbc_ctx* ctx, const void* v0, int steps, double* l
 /* In-place Chebyshev filter of degree ``degree`` on M_D^-1 H (Eq. chebfilt),
  * sigma-scaled: X <- T_m((H~ - c)/e) X / T_m((lmin - c)/e) with
  * c = (lmax + lT)/2, e = (lmax - lT)/2.  Requires lmin < lT < lmax, degree >= 1.
- * Each recurrence step is one H.X with the recurrence fused into the
- * assembly epilogue.  Uses library-owned workspace of two blocks. */
+ * Each recurrence step is one H.X followed by one fused elementwise kernel
+ * (M_D^-1 scaling, shift, three-term combination and reset of the H.X
+ * accumulator).  Uses library-owned workspace of two blocks. */
 gbc_status gbc_filter(gbc_ctx* ctx, void* X, int nvec, int ldx, int degree, double lT,
                       double lmax, double lmin, void* stream);
+
+/* Residual-split form of gbc_filter for a block of Ritz pairs (Sec. III.B.2:
+ * the filter reformulated with Hamiltonian-times-residual products so that
+ * they can run in lower precision; the exact formulation is in an unpublished
+ * manuscript, this is the reconstruction R11): with H^ = (M_D^-1 H - c)/e,
+ * Lambda^ = (ritz - c)/e and R = H^ X - X Lambda^,
+ *   X_m = X D_m + Z_m,  D_k = T_k(Lambda^)/T_k((lmin - c)/e) (diagonal, FP64),
+ *   Z_1 = sigma_1 R,  Z_{k+1} = 2 sigma_{k+1} H^ Z_k - sigma_k sigma_{k+1} Z_{k-1}
+ *                               + 2 sigma_{k+1} R D_k,
+ * which equals gbc_filter's result in exact arithmetic.  R is formed with the
+ * FP64 operator on an FP64 copy of X; the Z recurrence runs in the context
+ * precision, so its rounding error scales with ||R|| instead of ||X||.
+ * X must hold M_D-orthonormal Ritz vectors with Ritz values ``ritz`` (host,
+ * nvec doubles), e.g. from gbc_rayleigh_ritz.  In place; uses library-owned
+ * workspace (five blocks plus an FP64 block). */
+gbc_status gbc_filter_residual(gbc_ctx* ctx, void* X, int nvec, int ldx, int degree, double lT,
+                               double lmax, double lmin, const double* ritz, void* stream);
 
 /* Cholesky-Gram-Schmidt in the M_D inner product: S = X^H M_D X accumulated in
  * FP64, S = L L^H, X <- X L^-H.  GBC_ENOTPD if S is not positive definite

@@ -218,6 +218,80 @@ gbc_status rr_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, double* ritz, cudaStr
   return GBC_OK;
 }
 
+// Residual-split filter (Hamiltonian-times-residual form of the recurrence):
+// with H^ = (H~ - c)/e, Lambda^ = (Lambda - c)/e, R = H^ X - X Lambda^ and
+// D_k = T_k(Lambda^)/T_k(tau),  X_m = X D_m + Z_m,  Z_1 = sigma_1 R,
+// Z_{k+1} = 2 sigma_{k+1} H^ Z_k - sigma_k sigma_{k+1} Z_{k-1} + 2 sigma_{k+1} R D_k.
+// R is formed from an FP64 H.X of an FP64 copy of X; only the Z recurrence runs
+// in the context precision.  Work slots: 0 accumulator, 4 FP64 copy of X,
+// 5 FP64 H.X, 6 R, 7 / 1 the two Z buffers, 3 the per-column coefficient tables.
+template <typename T>
+gbc_status filter_split_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, int m, double lT,
+                          double lmax, double lmin, const double* ritz, cudaStream_t s) {
+  const double cc = 0.5 * (lmax + lT), e = 0.5 * (lmax - lT);
+  std::vector<double> sig(m);
+  sig[0] = e / (lmin - cc);
+  for (int k = 1; k < m; ++k) sig[k] = 1.0 / (2.0 / sig[0] - sig[k - 1]);
+  // per-column tables: lam_hat, g_k = 2 sigma_{k+1} D_k (k = 1..m-1), D_m
+  std::vector<double> lam(nvec), tab((size_t)(m + 1) * nvec, 0.0);
+  for (int v = 0; v < nvec; ++v) {
+    lam[v] = (ritz[v] - cc) / e;
+    double Dp = 1.0, Dc = sig[0] * lam[v];
+    for (int k = 1; k < m; ++k) {
+      tab[(size_t)(k - 1) * nvec + v] = 2.0 * sig[k] * Dc;
+      const double Dn = 2.0 * sig[k] * lam[v] * Dc - sig[k - 1] * sig[k] * Dp;
+      Dp = Dc;
+      Dc = Dn;
+    }
+    tab[(size_t)m * nvec + v] = Dc;
+    tab[(size_t)(m - 1) * nvec + v] = lam[v];
+  }
+  const size_t b64 = sizeof(double2) * 2 * (size_t)c->mesh.M * nvec;
+  const size_t bT = sizeof(cplx<T>) * 2 * (size_t)c->mesh.M * ldx;
+  GBC_TRY(gbc_ensure_work(c, 0, std::max(b64, bT)));
+  GBC_TRY(gbc_ensure_work(c, 4, b64));
+  GBC_TRY(gbc_ensure_work(c, 5, b64));
+  GBC_TRY(gbc_ensure_work(c, 6, bT));
+  GBC_TRY(gbc_ensure_work(c, 7, bT));
+  GBC_TRY(gbc_ensure_work(c, 1, bT));
+  GBC_TRY(gbc_ensure_work(c, 3, sizeof(double) * tab.size() + 256));
+  double* dtab = (double*)c->work[3];
+  GBC_CU(c, cudaMemcpyAsync(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s));
+  const double* d_lam = dtab + (size_t)(m - 1) * nvec;
+  const double* d_Dm = dtab + (size_t)m * nvec;
+  double2* X64 = (double2*)c->work[4];
+  double2* HX64 = (double2*)c->work[5];
+  cplx<T>* R = (cplx<T>*)c->work[6];
+  cplx<T>* Za = (cplx<T>*)c->work[7];
+  cplx<T>* Zb = (cplx<T>*)c->work[1];
+  cplx<T>* Y = (cplx<T>*)c->work[0];
+  // R and Z_1 from the FP64 operator
+  if (std::is_same<T, double>::value)
+    GBC_CU(c, launch_copy_block<double>((const double2*)X, X64, c->mesh.M, nvec, nvec, s));
+  else
+    GBC_CU(c, launch_convert_block((const float2*)X, ldx, X64, nvec, c->mesh.M, nvec, s));
+  GBC_TRY(apply_h_t<double>(c, X64, HX64, nvec, nvec, s));
+  GBC_CU(c, launch_split_init<T>(HX64, X64, c->d_invmd, d_lam, R, Za, c->mesh.M, nvec, ldx, nvec,
+                                 cc, 1.0 / e, sig[0], s));
+  // Z_0 = 0 lives in Zb
+  GBC_CU(c, cudaMemsetAsync(Zb, 0, bT, s));
+  GBC_CU(c, cudaMemsetAsync(Y, 0, bT, s));
+  const T* invmd = std::is_same<T, double>::value ? (const T*)c->d_invmd : (const T*)c->d_invmd32;
+  // Z_1 in Za, Z_0 in Zb; Z_{k+1} overwrites Z_{k-1}
+  for (int k = 1; k < m; ++k) {
+    cplx<T>* cur = (k & 1) ? Za : Zb;
+    cplx<T>* prev = (k & 1) ? Zb : Za;
+    GBC_TRY(apply_h_t<T>(c, cur, Y, nvec, ldx, s, false));
+    TimerScope ts(c, FAM_CHEB, s);
+    GBC_CU(c, launch_split_step<T>(Y, cur, prev, prev, R, invmd, dtab + (size_t)(k - 1) * nvec,
+                                   c->mesh.M, nvec, ldx, 2.0 * sig[k] / e, cc,
+                                   sig[k - 1] * sig[k], s));
+  }
+  cplx<T>* Zm = (m & 1) ? Za : Zb;
+  GBC_CU(c, launch_split_final<T>(X, Zm, d_Dm, c->mesh.M, nvec, ldx, s));
+  return GBC_OK;
+}
+
 // The mixed path keeps complex64 blocks for the filter but runs CholGS and
 // Rayleigh-Ritz on an FP64 copy (FP64 H.X, FP64 Gram, FP64 rotation): an FP32
 // H.X would put a first-order error eps32 * ||H~|| into X^H H X and hence into
@@ -278,7 +352,8 @@ void gbc_destroy(gbc_ctx* c) {
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
   void* ptrs[] = {c->d_md, c->d_invmd, c->d_invmd32, c->d_rawfields, c->d_fields64, c->d_fields32,
-                  c->work[0], c->work[1], c->work[2], c->work[3], c->work[4], c->d_small, c->d_flag};
+                  c->work[0], c->work[1], c->work[2], c->work[3], c->work[4], c->work[5],
+                  c->work[6], c->work[7], c->d_small, c->d_flag};
   for (void* p : ptrs) cudaFree(p);
   delete c;
 }
@@ -426,6 +501,21 @@ gbc_status gbc_filter(gbc_ctx* c, void* X, int nvec, int ldx, int degree, double
   if (nvec == 0) return GBC_OK;
   if (c->prec == GBC_FP64) return filter_t<double>(c, (double2*)X, nvec, ldx, degree, lT, lmax, lmin, s);
   return filter_t<float>(c, (float2*)X, nvec, ldx, degree, lT, lmax, lmin, s);
+}
+
+gbc_status gbc_filter_residual(gbc_ctx* c, void* X, int nvec, int ldx, int degree, double lT,
+                               double lmax, double lmin, const double* ritz, void* stream) {
+  if (!c) return GBC_EINVAL;
+  GBC_TRY(check_block(c, X, nvec, ldx));
+  if (!ritz) return gbc_fail(c, GBC_EINVAL, "null ritz");
+  if (degree < 1) return gbc_fail(c, GBC_EINVAL, "degree >= 1 required");
+  if (!(lmin < lT && lT < lmax)) return gbc_fail(c, GBC_EINVAL, "need lmin < lT < lmax");
+  GBC_TRY(gbc_prepare(c));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nvec == 0) return GBC_OK;
+  if (c->prec == GBC_FP64)
+    return filter_split_t<double>(c, (double2*)X, nvec, ldx, degree, lT, lmax, lmin, ritz, s);
+  return filter_split_t<float>(c, (float2*)X, nvec, ldx, degree, lT, lmax, lmin, ritz, s);
 }
 
 gbc_status gbc_cholgs(gbc_ctx* c, void* X, int nvec, int ldx, void* stream) {

@@ -176,6 +176,68 @@ __global__ void k_copy_block(const cplx<T>* __restrict__ X, cplx<T>* __restrict_
   }
 }
 
+// ---- residual-split recurrence (Hamiltonian-times-residual form) ------------------
+// R = ((M_D^-1 HX - c X)/e - X lam_hat[col]) from FP64 inputs, stored in T;
+// also Z1 = sigma1 R.
+template <typename T>
+__global__ void k_split_init(const double2* __restrict__ HX, const double2* __restrict__ X64,
+                             const double* __restrict__ invmd, const double* __restrict__ lam_hat,
+                             cplx<T>* __restrict__ R, cplx<T>* __restrict__ Z1, long long rows,
+                             int nvec, int ldx, int ld64, double c, double inv_e, double sigma1) {
+  const long long n = rows * (long long)nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nvec;
+    const int v = (int)(i - r * nvec);
+    const double w = invmd[r >> 1];
+    const double2 h = HX[r * ld64 + v], x = X64[r * ld64 + v];
+    const double lh = lam_hat[v];
+    const double rr = (w * h.x - c * x.x) * inv_e - lh * x.x;
+    const double ri = (w * h.y - c * x.y) * inv_e - lh * x.y;
+    R[r * ldx + v] = cmake<cplx<T>>(rr, ri);
+    Z1[r * ldx + v] = cmake<cplx<T>>(sigma1 * rr, sigma1 * ri);
+  }
+}
+
+// Zout = a (M_D^-1 Y - c Zcur) - b Zprev + g[col] R ; Y <- 0   (Zout may alias Zprev)
+template <typename T>
+__global__ void k_split_step(cplx<T>* __restrict__ Y, const cplx<T>* Zcur, const cplx<T>* Zprev,
+                             cplx<T>* Zout, const cplx<T>* __restrict__ R,
+                             const T* __restrict__ invmd, const double* __restrict__ g,
+                             long long rows, int nvec, int ldx, T a, T cshift, T b) {
+  const long long n = rows * (long long)nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nvec;
+    const int v = (int)(i - r * nvec);
+    const long long o = r * ldx + v;
+    const T w = invmd[r >> 1];
+    const cplx<T> y = Y[o], z = Zcur[o], zp = Zprev[o], rv = R[o];
+    const T gv = (T)g[v];
+    cplx<T> out;
+    out.x = a * (w * y.x - cshift * z.x) - b * zp.x + gv * rv.x;
+    out.y = a * (w * y.y - cshift * z.y) - b * zp.y + gv * rv.y;
+    Zout[o] = out;
+    Y[o] = cmake<cplx<T>>(0, 0);
+  }
+}
+
+// X = X D[col] + Z
+template <typename T>
+__global__ void k_split_final(cplx<T>* X, const cplx<T>* __restrict__ Z, const double* __restrict__ D,
+                              long long rows, int nvec, int ldx) {
+  const long long n = rows * (long long)nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nvec;
+    const int v = (int)(i - r * nvec);
+    const long long o = r * ldx + v;
+    const T d = (T)D[v];
+    const cplx<T> x = X[o], z = Z[o];
+    X[o] = cmake<cplx<T>>(d * x.x + z.x, d * x.y + z.y);
+  }
+}
+
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ X, int ldx, B* __restrict__ Out, int ldo,
                           long long rows, int nvec) {
@@ -316,6 +378,41 @@ cudaError_t launch_convert_block(const double2* X, int ldx, float2* Out, int ldo
   k_convert<double2, float2><<<grid_for(2 * M * nvec), 256, 0, s>>>(X, ldx, Out, ldo, 2 * M, nvec);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_split_init(const double2* HX, const double2* X64, const double* invmd,
+                              const double* lam_hat, cplx<T>* R, cplx<T>* Z1, long long M, int nvec,
+                              int ldx, int ld64, double c, double inv_e, double sigma1,
+                              cudaStream_t s) {
+  k_split_init<T><<<grid_for(2 * M * nvec), 256, 0, s>>>(HX, X64, invmd, lam_hat, R, Z1, 2 * M,
+                                                         nvec, ldx, ld64, c, inv_e, sigma1);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_split_step(cplx<T>* Y, const cplx<T>* Zcur, const cplx<T>* Zprev, cplx<T>* Zout,
+                              const cplx<T>* R, const T* invmd, const double* g, long long M,
+                              int nvec, int ldx, double a, double cshift, double b, cudaStream_t s) {
+  k_split_step<T><<<grid_for(2 * M * nvec), 256, 0, s>>>(Y, Zcur, Zprev, Zout, R, invmd, g, 2 * M,
+                                                         nvec, ldx, (T)a, (T)cshift, (T)b);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_split_final(cplx<T>* X, const cplx<T>* Z, const double* D, long long M, int nvec,
+                               int ldx, cudaStream_t s) {
+  k_split_final<T><<<grid_for(2 * M * nvec), 256, 0, s>>>(X, Z, D, 2 * M, nvec, ldx);
+  return cudaGetLastError();
+}
+#define INST_SPLIT(T)                                                                          \
+  template cudaError_t launch_split_init<T>(const double2*, const double2*, const double*,     \
+                                            const double*, cplx<T>*, cplx<T>*, long long, int, \
+                                            int, int, double, double, double, cudaStream_t);   \
+  template cudaError_t launch_split_step<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*, \
+                                            const cplx<T>*, const T*, const double*, long long, \
+                                            int, int, double, double, double, cudaStream_t);   \
+  template cudaError_t launch_split_final<T>(cplx<T>*, const cplx<T>*, const double*, long long, \
+                                             int, int, cudaStream_t);
+INST_SPLIT(float)
+INST_SPLIT(double)
 
 cudaError_t launch_mdot(const double2* a, const double2* b, const double* md, long long n,
                         double2* out, cudaStream_t s) {

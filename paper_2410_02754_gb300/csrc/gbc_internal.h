@@ -96,11 +96,15 @@ struct ProjDev {
   // chunk table for the projection kernel: (atom, first node, count)
   int nchunks = 0;
   int4* d_chunks = nullptr;
-  // node-centric expansion: unique support nodes and their (atom, position) incidences
+  // expansion: every distinct support node is owned by the lowest-index atom
+  // holding it; owned nodes grouped by owner, with the other atoms' incidences
   long long nuniq = 0;
-  long long* d_uniq_node = nullptr;  // [nuniq]
-  int* d_uniq_ptr = nullptr;         // [nuniq+1]
-  int2* d_uniq_inc = nullptr;        // [nnodes_total] (atom, position in atom list)
+  long long* d_own_node = nullptr;   // [nuniq] free node index
+  int* d_own_pos = nullptr;          // [nuniq] row in the owner's P table
+  int* d_own_xptr = nullptr;         // [nuniq+1] CSR into d_own_xinc
+  int2* d_own_xinc = nullptr;        // other (atom, row) incidences
+  int nexp_chunks = 0;
+  int4* d_exp_chunks = nullptr;      // (owner atom, first owned index, count, 0)
   // raw inputs kept on device for recomputation at a new k
   double* d_pvals = nullptr;
   int* d_entry_cell = nullptr;
@@ -130,8 +134,8 @@ struct gbc_ctx {
   float* d_fields32 = nullptr;
   ProjDev proj;
   // workspaces
-  void* work[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t work_bytes[5] = {0, 0, 0, 0, 0};
+  void* work[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t work_bytes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   void* d_small = nullptr;           // small dense scratch (Gram, eigensolver)
   size_t small_bytes = 0;
   int* d_flag = nullptr;
@@ -204,6 +208,19 @@ cudaError_t launch_gram(const cplx<T>* X, const cplx<T>* Y, const double* md, lo
 template <typename T>
 cudaError_t launch_rotate(const cplx<T>* X, const double2* Q, cplx<T>* Out, long long M, int nvec,
                           int ldx, cudaStream_t s);
+// residual-split filter kernels
+template <typename T>
+cudaError_t launch_split_init(const double2* HX, const double2* X64, const double* invmd,
+                              const double* lam_hat, cplx<T>* R, cplx<T>* Z1, long long M, int nvec,
+                              int ldx, int ld64, double c, double inv_e, double sigma1,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_split_step(cplx<T>* Y, const cplx<T>* Zcur, const cplx<T>* Zprev, cplx<T>* Zout,
+                              const cplx<T>* R, const T* invmd, const double* g, long long M,
+                              int nvec, int ldx, double a, double cshift, double b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_split_final(cplx<T>* X, const cplx<T>* Z, const double* D, long long M, int nvec,
+                               int ldx, cudaStream_t s);
 // block precision conversion (float2 <-> double2), rows of 2M, nvec columns
 cudaError_t launch_convert_block(const float2* X, int ldx, double2* Out, int ldo, long long M,
                                  int nvec, cudaStream_t s);

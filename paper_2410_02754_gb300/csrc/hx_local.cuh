@@ -55,8 +55,11 @@ hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
   constexpr int BUF = (NQ + 1) * (NQ + 1) * NQ;      // points per padded buffer
   constexpr int NQ3 = NQ * NQ * NQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);             // [VB][3][BUF][2]
-  T* fld = reinterpret_cast<T*>(buf + VB * 3 * BUF * 2);   // [4][NQ3]
+  // per-vector stride 3*BUF*2 + 1 complex: the 8-byte shift puts the vectors of a
+  // CTA (adjacent threads) in different shared-memory banks
+  constexpr int VSTRIDE = 3 * BUF * 2 + 1;
+  C* buf = reinterpret_cast<C*>(smem_raw);             // [VB][VSTRIDE]
+  T* fld = reinterpret_cast<T*>(buf + VB * VSTRIDE);   // [4][NQ3]
 
   const int v = threadIdx.x % VB;
   const int lane = threadIdx.x / VB;
@@ -67,9 +70,9 @@ hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
   const int nx = a.mesh.ncell[0], ny = a.mesh.ncell[1];
   const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
 
-  C* A = buf + (v * 3 + 0) * BUF * 2;
-  C* Bb = buf + (v * 3 + 1) * BUF * 2;
-  C* Cb = buf + (v * 3 + 2) * BUF * 2;
+  C* A = buf + v * VSTRIDE;
+  C* Bb = A + BUF * 2;
+  C* Cb = A + 2 * BUF * 2;
 
   // ---- fields of this cell (shared by all VB vectors)
   const T* fsrc = a.fields + (size_t)e * 4 * NQ3;
@@ -336,7 +339,7 @@ hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
 }
 
 template <typename T, int NP, int NQ, int VB> constexpr size_t hx_local_smem() {
-  return sizeof(cplx<T>) * (size_t)VB * 3 * ((NQ + 1) * (NQ + 1) * NQ) * 2 +
+  return sizeof(cplx<T>) * (size_t)VB * (3 * ((NQ + 1) * (NQ + 1) * NQ) * 2 + 1) +
          sizeof(T) * 4 * NQ * NQ * NQ;
 }
 

@@ -30,8 +30,7 @@ __device__ __forceinline__ void catomic(double2* p, double2 v) {
   atomicAdd(&p->y, v.y);
 }
 
-constexpr int kChunk = 512;     // support nodes per projection block
-constexpr int kStage = 32;      // nodes staged in shared memory at a time
+constexpr int kStage = 64;      // support nodes staged in shared memory at a time
 constexpr int kCols = 128;      // threads (columns) per block
 
 // C[(c_off + 2chi + s) * nvec + v] += sum_j conj(P[j][chi]) X[node_j][s][v]
@@ -63,11 +62,18 @@ nl_project(const cplx<T>* __restrict__ X, int ldx, int nvec, const int4* __restr
     for (int t = threadIdx.x; t < nb; t += kCols) Ns[t] = nodes[noff + j0 + jb + t];
     __syncthreads();
     if (ok) {
-      for (int t = 0; t < nb; ++t) {
-        const C x = X[(Ns[t] * 2 + s) * ldx + v];
+      for (int t = 0; t < nb; t += 4) {
+        C x[4];
 #pragma unroll
-        for (int c = 0; c < MAXPJ; ++c)
-          if (c < npj) cmac_conj(acc[c], Ps[t][c], x);
+        for (int u = 0; u < 4; ++u)
+          x[u] = (t + u < nb) ? X[(Ns[t + u] * 2 + s) * ldx + v] : cmake<C>(0, 0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (t + u >= nb) break;
+#pragma unroll
+          for (int c = 0; c < MAXPJ; ++c)
+            if (c < npj) cmac_conj(acc[c], Ps[t + u][c], x[u]);
+        }
       }
     }
     __syncthreads();
@@ -99,36 +105,62 @@ __global__ void nl_couple(const cplx<T>* __restrict__ Cbuf, cplx<T>* __restrict_
   Cp[base + (size_t)r * nvec] = acc;
 }
 
-// Y[node][s][v] += sum over atoms whose support holds node of sum_chi P[pos][chi] Cp[2chi+s][v]
-// A block owns kExpNodes consecutive unique support nodes and 128 columns.
-constexpr int kExpNodes = 16;
-template <typename T>
+// Y[node][s][v] += sum over atoms whose support holds node of sum_chi P[pos][chi] Cp[2chi+s][v].
+// Every distinct support node is owned by the lowest-index atom whose support
+// holds it; the owner's block writes it once (plain read-modify-write, no
+// atomics) and adds the other atoms' terms from their incidence list.  The
+// owner's C' column stays in registers, the staged P rows in shared memory.
+constexpr int kExpStage = 32;
+template <typename T, int MAXPJ>
 __global__ void __launch_bounds__(kCols)
-nl_expand(cplx<T>* __restrict__ Y, int ldx, int nvec, const long long* __restrict__ uniq_node,
-          const int* __restrict__ uniq_ptr, const int2* __restrict__ uniq_inc, long long nuniq,
+nl_expand(cplx<T>* __restrict__ Y, int ldx, int nvec, const int4* __restrict__ chunks,
+          const long long* __restrict__ own_node, const int* __restrict__ own_pos,
+          const int* __restrict__ own_xptr, const int2* __restrict__ own_xinc,
           const cplx<T>* __restrict__ P, const int* __restrict__ atom_npj,
           const int* __restrict__ atom_pv_off, const int* __restrict__ atom_c_off,
           const cplx<T>* __restrict__ Cp) {
   using C = cplx<T>;
-  const long long u0 = (long long)blockIdx.x * kExpNodes;
-  const long long u1 = min(nuniq, u0 + kExpNodes);
+  __shared__ C Ps[kExpStage][MAXPJ];
+  const int4 ch = chunks[blockIdx.x];       // (atom, first owned index, count, -)
+  const int atom = ch.x, u0 = ch.y, cnt = ch.z;
+  const int npj = atom_npj[atom];
+  const C* Pa = P + atom_pv_off[atom];
   const int col = blockIdx.y * kCols + threadIdx.x;
-  if (col >= 2 * nvec) return;
-  const int s = col / nvec, v = col % nvec;
-  for (long long u = u0; u < u1; ++u) {
-    C acc = cmake<C>(0, 0);
-    for (int k = uniq_ptr[u]; k < uniq_ptr[u + 1]; ++k) {
-      const int2 inc = uniq_inc[k];
-      const int npj = atom_npj[inc.x];
-      const C* Pr = P + atom_pv_off[inc.x] + (size_t)inc.y * npj;
-      const C* Cr = Cp + (size_t)atom_c_off[inc.x] * nvec + v + (size_t)s * nvec;
-      for (int c = 0; c < npj; ++c) cmac(acc, Pr[c], Cr[(size_t)(2 * c) * nvec]);
+  const bool ok = col < 2 * nvec;
+  const int s = ok ? col / nvec : 0, v = ok ? col % nvec : 0;
+  C cp[MAXPJ];
+  const C* Ca = Cp + (size_t)(atom_c_off[atom] + s) * nvec + v;
+#pragma unroll
+  for (int c = 0; c < MAXPJ; ++c) cp[c] = (ok && c < npj) ? Ca[(size_t)(2 * c) * nvec] : cmake<C>(0, 0);
+  for (int jb = 0; jb < cnt; jb += kExpStage) {
+    const int nb = min(kExpStage, cnt - jb);
+    for (int t = threadIdx.x; t < nb * npj; t += kCols) {
+      const int jj = t / npj, c = t % npj;
+      Ps[jj][c] = Pa[(size_t)own_pos[u0 + jb + jj] * npj + c];
     }
-    C* y = &Y[(uniq_node[u] * 2 + s) * ldx + v];
-    C o = *y;
-    o.x += acc.x;
-    o.y += acc.y;
-    *y = o;
+    __syncthreads();
+    if (ok) {
+      for (int t = 0; t < nb; ++t) {
+        const int u = u0 + jb + t;
+        C acc = cmake<C>(0, 0);
+#pragma unroll
+        for (int c = 0; c < MAXPJ; ++c)
+          if (c < npj) cmac(acc, Ps[t][c], cp[c]);
+        for (int k = own_xptr[u]; k < own_xptr[u + 1]; ++k) {
+          const int2 inc = own_xinc[k];
+          const int nb2 = atom_npj[inc.x];
+          const C* Pr = P + atom_pv_off[inc.x] + (size_t)inc.y * nb2;
+          const C* Cr = Cp + (size_t)(atom_c_off[inc.x] + s) * nvec + v;
+          for (int c = 0; c < nb2; ++c) cmac(acc, Pr[c], Cr[(size_t)(2 * c) * nvec]);
+        }
+        C* y = &Y[(own_node[u] * 2 + s) * ldx + v];
+        C o = *y;
+        o.x += acc.x;
+        o.y += acc.y;
+        *y = o;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -151,7 +183,7 @@ template <typename T>
 cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx,
                             cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s) {
   const ProjDev& pj = c->proj;
-  if (pj.natoms == 0 || nvec == 0 || pj.nchunks == 0 || pj.nuniq == 0) return cudaSuccess;
+  if (pj.natoms == 0 || nvec == 0 || pj.nchunks == 0 || pj.nexp_chunks == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(Cbuf, 0, sizeof(cplx<T>) * (size_t)pj.rows_total * nvec, s);
   if (e != cudaSuccess) return e;
   if (pj.max_npj <= 4) e = run_project<T, 4>(c, X, nvec, ldx, Cbuf, s);
@@ -168,10 +200,16 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
   if (e != cudaSuccess) return e;
   const cplx<T>* P = std::is_same<T, double>::value ? (const cplx<T>*)pj.d_P64
                                                     : (const cplx<T>*)pj.d_P32;
-  dim3 g3((unsigned)((pj.nuniq + kExpNodes - 1) / kExpNodes), (2 * nvec + kCols - 1) / kCols);
-  nl_expand<T><<<g3, kCols, 0, s>>>(Y, ldx, nvec, pj.d_uniq_node, pj.d_uniq_ptr, pj.d_uniq_inc,
-                                   pj.nuniq, P, pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off,
-                                   Cpbuf);
+  dim3 g3((unsigned)pj.nexp_chunks, (2 * nvec + kCols - 1) / kCols);
+#define GBC_EXPAND(MP)                                                                        \
+  nl_expand<T, MP><<<g3, kCols, 0, s>>>(Y, ldx, nvec, pj.d_exp_chunks, pj.d_own_node,           \
+                                        pj.d_own_pos, pj.d_own_xptr, pj.d_own_xinc, P,         \
+                                        pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off, Cpbuf)
+  if (pj.max_npj <= 4) GBC_EXPAND(4);
+  else if (pj.max_npj <= 8) GBC_EXPAND(8);
+  else if (pj.max_npj <= 18) GBC_EXPAND(18);
+  else GBC_EXPAND(GBC_MAX_NPJ);
+#undef GBC_EXPAND
   return cudaGetLastError();
 }
 

@@ -433,8 +433,8 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
       }
       pvals_total += nq3 * npj[a];
     }
-    for (size_t j = 0; j < nodes.size(); j += 512) {
-      const int cnt = (int)std::min<size_t>(512, nodes.size() - j);
+    for (size_t j = 0; j < nodes.size(); j += 1024) {
+      const int cnt = (int)std::min<size_t>(1024, nodes.size() - j);
       chunks.push_back(make_int4(a, (int)j, cnt, pj.node_off[a]));
     }
     for (size_t j = 0; j < nodes.size(); ++j) inc.push_back({nodes[j], make_int2(a, (int)j)});
@@ -451,18 +451,43 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
                    [](const std::pair<long long, int2>& x, const std::pair<long long, int2>& y) {
                      return x.first < y.first;
                    });
-  std::vector<long long> uniq;
-  std::vector<int> uptr;
-  std::vector<int2> uinc;
-  for (size_t i = 0; i < inc.size(); ++i) {
-    if (uniq.empty() || uniq.back() != inc[i].first) {
-      uniq.push_back(inc[i].first);
-      uptr.push_back((int)uinc.size());
-    }
-    uinc.push_back(inc[i].second);
+  // group the distinct support nodes by owner (lowest atom index holding the
+  // node: the stable sort keeps incidences of a node in atom order)
+  std::vector<std::vector<long long>> own_node(natoms);
+  std::vector<std::vector<int>> own_pos(natoms);
+  std::vector<std::vector<std::vector<int2>>> own_extra(natoms);
+  for (size_t i = 0; i < inc.size();) {
+    size_t j = i;
+    while (j < inc.size() && inc[j].first == inc[i].first) ++j;
+    const int owner = inc[i].second.x;
+    own_node[owner].push_back(inc[i].first);
+    own_pos[owner].push_back(inc[i].second.y);
+    std::vector<int2> ex;
+    for (size_t k = i + 1; k < j; ++k) ex.push_back(inc[k].second);
+    own_extra[owner].push_back(ex);
+    i = j;
   }
-  uptr.push_back((int)uinc.size());
-  pj.nuniq = (long long)uniq.size();
+  std::vector<long long> onode;
+  std::vector<int> opos, oxptr;
+  std::vector<int2> oxinc;
+  std::vector<int4> echunks;
+  for (int a = 0; a < natoms; ++a) {
+    const int first = (int)onode.size();
+    for (size_t j = 0; j < own_node[a].size(); ++j) {
+      onode.push_back(own_node[a][j]);
+      opos.push_back(own_pos[a][j]);
+      oxptr.push_back((int)oxinc.size());
+      for (const int2& e : own_extra[a][j]) oxinc.push_back(e);
+    }
+    for (size_t j = 0; j < own_node[a].size(); j += 512) {
+      const int cnt = (int)std::min<size_t>(512, own_node[a].size() - j);
+      echunks.push_back(make_int4(a, first + (int)j, cnt, 0));
+    }
+  }
+  oxptr.push_back((int)oxinc.size());
+  if (oxinc.empty()) oxinc.push_back(make_int2(0, 0));   // keep a valid allocation
+  pj.nuniq = (long long)onode.size();
+  pj.nexp_chunks = (int)echunks.size();
 
   std::vector<float2> d32(pj.delta_off[natoms] > 0 ? pj.delta_off[natoms] : 0);
   for (size_t i = 0; i < d32.size(); ++i)
@@ -477,9 +502,11 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
   GBC_TRY(upload(c, (void**)&pj.d_delta64, delta, sizeof(double2) * pj.delta_off[natoms]));
   GBC_TRY(upload(c, (void**)&pj.d_delta32, d32.data(), sizeof(float2) * d32.size()));
   GBC_TRY(upload(c, (void**)&pj.d_chunks, chunks.data(), sizeof(int4) * chunks.size()));
-  GBC_TRY(upload(c, (void**)&pj.d_uniq_node, uniq.data(), sizeof(long long) * uniq.size()));
-  GBC_TRY(upload(c, (void**)&pj.d_uniq_ptr, uptr.data(), sizeof(int) * uptr.size()));
-  GBC_TRY(upload(c, (void**)&pj.d_uniq_inc, uinc.data(), sizeof(int2) * uinc.size()));
+  GBC_TRY(upload(c, (void**)&pj.d_own_node, onode.data(), sizeof(long long) * onode.size()));
+  GBC_TRY(upload(c, (void**)&pj.d_own_pos, opos.data(), sizeof(int) * opos.size()));
+  GBC_TRY(upload(c, (void**)&pj.d_own_xptr, oxptr.data(), sizeof(int) * oxptr.size()));
+  GBC_TRY(upload(c, (void**)&pj.d_own_xinc, oxinc.data(), sizeof(int2) * oxinc.size()));
+  GBC_TRY(upload(c, (void**)&pj.d_exp_chunks, echunks.data(), sizeof(int4) * echunks.size()));
   GBC_TRY(upload(c, (void**)&pj.d_pvals, pvals, sizeof(double) * pvals_total));
   GBC_TRY(upload(c, (void**)&pj.d_entry_cell, entry_cell.data(), sizeof(int) * entry_cell.size()));
   GBC_TRY(upload(c, (void**)&pj.d_entry_img, entry_img.data(), sizeof(int) * entry_img.size()));
@@ -498,7 +525,8 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
 void free_projectors(ProjDev& pj) {
   void* ptrs[] = {pj.d_nodes, pj.d_atom_npj, pj.d_atom_node_off, pj.d_atom_pv_off,
                   pj.d_atom_delta_off, pj.d_atom_c_off, pj.d_P64, pj.d_P32, pj.d_delta64,
-                  pj.d_delta32, pj.d_chunks, pj.d_uniq_node, pj.d_uniq_ptr, pj.d_uniq_inc,
+                  pj.d_delta32, pj.d_chunks, pj.d_own_node, pj.d_own_pos, pj.d_own_xptr,
+                  pj.d_own_xinc, pj.d_exp_chunks,
                   pj.d_pvals, pj.d_entry_cell, pj.d_entry_img, pj.d_entry_atom, pj.d_entry_pos};
   for (void* p : ptrs) cudaFree(p);
   pj = ProjDev();

@@ -25,6 +25,7 @@ STATUS = {0: "GBC_OK", 1: "GBC_EINVAL", 2: "GBC_ENOMEM", 3: "GBC_ECUDA", 4: "GBC
 EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_set_mesh",
            "gbc_set_kpoint", "gbc_set_fields", "gbc_set_projectors", "gbc_set_precision",
            "gbc_get_nnodes", "gbc_get_mass", "gbc_apply_h", "gbc_lanczos_bounds", "gbc_filter",
+           "gbc_filter_residual",
            "gbc_cholgs", "gbc_rayleigh_ritz", "gbc_set_timing", "gbc_get_timing"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
@@ -64,6 +65,7 @@ def load_library(path: str = LIB_PATH):
         "gbc_lanczos_bounds": ([P, V, I, DP, DP, V], I),
         "gbc_filter": ([P, V, I, I, I, D, D, D, V], I),
         "gbc_cholgs": ([P, V, I, I, V], I),
+        "gbc_filter_residual": ([P, V, I, I, I, D, D, D, DP, V], I),
         "gbc_rayleigh_ritz": ([P, V, I, I, DP, V], I),
         "gbc_set_timing": ([P, I], I),
         "gbc_get_timing": ([P, I, DP, ct.POINTER(ct.c_longlong)], I),
@@ -199,6 +201,15 @@ class Context:
         nvec = ldx if nvec is None else nvec
         self._chk(self.lib.gbc_filter(self.h, px, int(nvec), int(ldx), int(degree), float(lT),
                                       float(lmax), float(lmin), _stream_ptr(stream)))
+
+    def filter_residual(self, X, degree, lT, lmax, lmin, ritz, nvec=None, stream=None):
+        """Residual-split filter of a block of Ritz pairs (X, ritz)."""
+        px, ldx = self._block(X)
+        nvec = ldx if nvec is None else nvec
+        r, rp = _darr(np.asarray(ritz, np.float64)[:nvec])
+        self._chk(self.lib.gbc_filter_residual(self.h, px, int(nvec), int(ldx), int(degree),
+                                               float(lT), float(lmax), float(lmin), rp,
+                                               _stream_ptr(stream)))
 
     def cholgs(self, X, nvec=None, stream=None):
         px, ldx = self._block(X)

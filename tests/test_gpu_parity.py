@@ -207,3 +207,51 @@ def test_c1_full_size_sampled_rows(g):
         got = Yd[torch.from_numpy(rows).cuda()].cpu().numpy()
         assert rel(got, ref) < tol, (prec, rel(got, ref))
         ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
+def test_residual_split_filter_matches_oracle(g, prec, tol):
+    prob = syn.make_problem(ncell=(3, 2, 2), h=(1.1, 1.1, 1.1), p=4, k=(0.1, 0.2, -0.1),
+                            natoms=2, rc=1.2, seed=3)
+    d = fe.Discretisation(prob)
+    X = oc.cholgs(syn.random_block(d.mesh.nnodes, 6, 4), d.md)
+    ritz, X, HX = oc.rayleigh_ritz(d.apply_h, X)
+    lT, lmax, lmin = float(ritz[-1]), 120.0, float(ritz[0]) - 0.5
+    for m in (1, 2, 9):
+        ref = oc.cheb_filter_split(d.apply_htilde, X, ritz, m, lT, lmax, lmin,
+                                   HtX=HX / d.md[:, None, None])
+        ctx = make_ctx(g, prob, prec)
+        Xd = to_dev(X, prec)
+        ctx.filter_residual(Xd, m, lT, lmax, lmin, ritz)
+        torch.cuda.synchronize()
+        assert rel(Xd.cpu().numpy(), ref) < tol, (m, rel(Xd.cpu().numpy(), ref))
+        ctx.close()
+
+
+def test_residual_split_reduces_fp32_error_near_convergence(g):
+    """For nearly converged Ritz pairs the FP32 residual-split filter is far
+    closer to the FP64 filter than the direct FP32 recurrence."""
+    prob = syn.make_problem(ncell=(2, 2, 2), h=(1.2, 1.2, 1.2), p=4, k=(0.1, 0.0, 0.2),
+                            natoms=2, rc=1.2, seed=6)
+    d = fe.Discretisation(prob)
+    M = d.mesh.nnodes
+    lmin, lmax = oc.lanczos_bounds(d.apply_htilde, d.md, syn.random_start(M, 1), 20)
+    hist, X = oc.chfsi(d.apply_h, d.md, syn.random_block(M, 10, 2), cycles=12, degree=12,
+                       lmin=lmin, lmax=lmax)
+    ritz, X, HX = oc.rayleigh_ritz(d.apply_h, X)
+    lT, lo = float(ritz[-1]), min(lmin, float(ritz[0]))
+    ref = oc.cheb_filter(d.apply_htilde, X, 15, lT, lmax, lo)
+    errs = {}
+    for mode in ("direct", "split"):
+        ctx = make_ctx(g, prob, 1)
+        Xd = to_dev(X, 1)
+        if mode == "direct":
+            ctx.filter(Xd, 15, lT, lmax, lo)
+        else:
+            ctx.filter_residual(Xd, 15, lT, lmax, lo, ritz)
+        torch.cuda.synchronize()
+        got = Xd.cpu().numpy().astype(np.complex128)
+        # error in the part orthogonal to the exact result's span direction per column
+        errs[mode] = rel(got, ref)
+        ctx.close()
+    assert errs["split"] < 0.2 * errs["direct"], errs
