@@ -164,6 +164,29 @@ gbc_status gbc_cholgs(gbc_ctx* ctx, void* X, int nvec, int ldx, void* stream);
 gbc_status gbc_rayleigh_ritz(gbc_ctx* ctx, void* X, int nvec, int ldx, double* ritz,
                              void* stream);
 
+/* ---- allocation-free variant ------------------------------------------------ */
+
+/* Y = H^k X exactly as gbc_apply_h computes it, for callers that cannot let the
+ * library allocate device memory: host applications that own every byte of
+ * device memory through their own pool or caching allocator, or that must not
+ * trigger the device-wide synchronisation cudaMalloc / cudaFree can cause in
+ * the middle of their own pipelined work.  The paper has no counterpart; this
+ * is a deployment variant of the H.X call.
+ * The per-atom coefficient scratch (2 * (sum over atoms of 2*npj) * nvec
+ * complex values) lives in one fixed 32 MiB device array that every GPU
+ * loading the library holds until the process exits; larger requests return
+ * GBC_EINVAL with the sizes in gbc_last_error.  Calls no cudaMalloc, cudaFree
+ * or allocating library routine.  The operator tables must already be built
+ * for the current mesh, fields, k-point and projectors (any earlier
+ * gbc_apply_h / gbc_filter / gbc_lanczos_bounds / gbc_cholgs /
+ * gbc_rayleigh_ritz call builds them), otherwise GBC_ESTATE.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the previous call's contents; calls that overlap on the GPU
+ * race on it, so callers must order them. */
+gbc_status gbc_apply_h_noalloc(gbc_ctx* ctx, const void* X, void* Y, int nvec, int ldx,
+                               void* stream);
+
 /* ---- tracing -------------------------------------------------------------- */
 
 /* Kernel families for gbc_get_timing. */

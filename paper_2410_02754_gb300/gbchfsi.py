@@ -26,7 +26,8 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_set_kpoint", "gbc_set_fields", "gbc_set_projectors", "gbc_set_precision",
            "gbc_get_nnodes", "gbc_get_mass", "gbc_apply_h", "gbc_lanczos_bounds", "gbc_filter",
            "gbc_filter_residual",
-           "gbc_cholgs", "gbc_rayleigh_ritz", "gbc_set_timing", "gbc_get_timing"]
+           "gbc_cholgs", "gbc_rayleigh_ritz", "gbc_set_timing", "gbc_get_timing",
+           "gbc_apply_h_noalloc"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -68,6 +69,7 @@ def load_library(path: str = LIB_PATH):
         "gbc_filter_residual": ([P, V, I, I, I, D, D, D, DP, V], I),
         "gbc_rayleigh_ritz": ([P, V, I, I, DP, V], I),
         "gbc_set_timing": ([P, I], I),
+        "gbc_apply_h_noalloc": ([P, V, V, I, I, V], I),
         "gbc_get_timing": ([P, I, DP, ct.POINTER(ct.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
@@ -195,6 +197,17 @@ class Context:
             raise ValueError("X and Y need the same ldx")
         nvec = ldx if nvec is None else nvec
         self._chk(self.lib.gbc_apply_h(self.h, px, py, int(nvec), int(ldx), _stream_ptr(stream)))
+
+    def apply_h_noalloc(self, X, Y, nvec=None, stream=None):
+        """H.X without any device allocation by the library (fixed 32 MiB
+        scratch); the tables must have been built by an earlier call."""
+        px, ldx = self._block(X)
+        py, ldy = self._block(Y)
+        if ldx != ldy:
+            raise ValueError("X and Y need the same ldx")
+        nvec = ldx if nvec is None else nvec
+        self._chk(self.lib.gbc_apply_h_noalloc(self.h, px, py, int(nvec), int(ldx),
+                                               _stream_ptr(stream)))
 
     def filter(self, X, degree, lT, lmax, lmin, nvec=None, stream=None):
         px, ldx = self._block(X)
