@@ -17,6 +17,7 @@
 // n_q^3 shared-memory buffers; per-point data are the two spin components.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "gbc_internal.h"
@@ -48,7 +49,7 @@ template <int NQ> __device__ __forceinline__ int pidx(int x, int y, int z) {
 }
 
 template <typename T, int NP, int NQ, bool KPT, int VB>
-__global__ void __launch_bounds__(VB * 64)
+__global__ void __launch_bounds__(VB * 64, sizeof(T) == 4 ? 3 : 2)
 hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
   using C = cplx<T>;
   constexpr int TPV = 64;
@@ -64,34 +65,72 @@ hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
   const int v = threadIdx.x % VB;
   const int lane = threadIdx.x / VB;
   const int vchunks = (a.nvec + VB - 1) / VB;
-  const int e = blockIdx.x / vchunks;
-  const int vec = (blockIdx.x % vchunks) * VB + v;
-  const bool vok = vec < a.nvec;
+  const long long nitems = (long long)a.mesh.E * vchunks;
   const int nx = a.mesh.ncell[0], ny = a.mesh.ncell[1];
-  const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
 
   C* A = buf + v * VSTRIDE;
   C* Bb = A + BUF * 2;
   C* Cb = A + 2 * BUF * 2;
 
-  // ---- fields of this cell (shared by all VB vectors)
-  const T* fsrc = a.fields + (size_t)e * 4 * NQ3;
-  for (int i = threadIdx.x; i < 4 * NQ3; i += blockDim.x) fld[i] = fsrc[i];
-
-  // ---- extract X^(e) (both spins) into A
-  for (int i = lane; i < NP * NP * NP; i += TPV) {
-    const int ix = i % NP, iy = (i / NP) % NP, iz = i / (NP * NP);
-    const long long I = gbc_node(a.mesh, cx, cy, cz, ix, iy, iz);
-    C u = cmake<C>(0, 0), d = cmake<C>(0, 0);
-    if (I >= 0 && vok) {
-      u = a.X[(I * 2 + 0) * a.ldx + vec];
-      d = a.X[(I * 2 + 1) * a.ldx + vec];
+  // Persistent CTA: items (cell, vector chunk), vector chunk fastest, taken with a
+  // grid stride so the CTAs running together work on neighbouring cells.  The next
+  // item's X^(e) and fields are loaded into registers while the current one is
+  // computed (the loads are issued right after the current item is staged).
+  constexpr int PPL = (NP * NP * NP + TPV - 1) / TPV;       // nodes per lane
+  constexpr int FPT = (4 * NQ3 + VB * TPV - 1) / (VB * TPV); // field values per thread
+  C pfx[PPL][2];
+  T pff[FPT];
+  auto prefetch = [&](long long it) {
+    if (it >= nitems) return;
+    const int e = (int)(it / vchunks);
+    const int vec = (int)(it % vchunks) * VB + v;
+    const bool vok = vec < a.nvec;
+    const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
+#pragma unroll
+    for (int j = 0; j < PPL; ++j) {
+      const int i = lane + j * TPV;
+      pfx[j][0] = cmake<C>(0, 0);
+      pfx[j][1] = cmake<C>(0, 0);
+      if (i < NP * NP * NP && vok) {
+        const long long I = gbc_node(a.mesh, cx, cy, cz, i % NP, (i / NP) % NP, i / (NP * NP));
+        if (I >= 0) {
+          pfx[j][0] = a.X[(I * 2 + 0) * a.ldx + vec];
+          pfx[j][1] = a.X[(I * 2 + 1) * a.ldx + vec];
+        }
+      }
     }
-    const int q = pidx<NQ>(ix, iy, iz);
-    A[2 * q] = u;
-    A[2 * q + 1] = d;
+    const T* fsrc = a.fields + (size_t)e * 4 * NQ3;
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+      const int f = threadIdx.x + j * VB * TPV;
+      pff[j] = f < 4 * NQ3 ? fsrc[f] : (T)0;
+    }
+  };
+  prefetch(blockIdx.x);
+
+  for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+  const int e = (int)(item / vchunks);
+  const int vec = (int)(item % vchunks) * VB + v;
+  const bool vok = vec < a.nvec;
+  const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
+
+  // ---- stage X^(e) (both spins) and the cell's fields from the prefetch registers
+#pragma unroll
+  for (int j = 0; j < PPL; ++j) {
+    const int i = lane + j * TPV;
+    if (i < NP * NP * NP) {
+      const int q = pidx<NQ>(i % NP, (i / NP) % NP, i / (NP * NP));
+      A[2 * q] = pfx[j][0];
+      A[2 * q + 1] = pfx[j][1];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < FPT; ++j) {
+    const int f = threadIdx.x + j * VB * TPV;
+    if (f < 4 * NQ3) fld[f] = pff[j];
   }
   __syncthreads();
+  prefetch(item + gridDim.x);
 
   // ===== kinetic / k part:  Y = G_x(B_y B_z X) + B_x(G_y B_z X + B_y G_z X)
   // z-stage: T1 = B_z X -> Bb, T2 = G_z X -> Cb
@@ -336,6 +375,7 @@ hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
       }
     }
   }
+  }  // item loop
 }
 
 template <typename T, int NP, int NQ, int VB> constexpr size_t hx_local_smem() {
@@ -376,18 +416,28 @@ cudaError_t launch_hx_local_p(const gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, in
   const auto tb = make_tables<T, NP, NQ>(c);
   const bool kpt = (c->k[0] != 0.0 || c->k[1] != 0.0 || c->k[2] != 0.0);
   constexpr size_t smem = hx_local_smem<T, NP, NQ, VB>();
-  const long long nblk = (long long)c->mesh.E * ((nvec + VB - 1) / VB);
-  if (nblk <= 0) return cudaSuccess;
-  if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const long long nitems = (long long)c->mesh.E * ((nvec + VB - 1) / VB);
+  if (nitems <= 0) return cudaSuccess;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (err != cudaSuccess) return err;
   if (kpt) {
     auto k = hx_local_kernel<T, NP, NQ, true, VB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, VB * 64, smem);
+    if (e != cudaSuccess) return e;
+    const long long nblk = std::min<long long>(nitems, (long long)nsm * std::max(per_sm, 1));
     k<<<(unsigned)nblk, VB * 64, smem, s>>>(a, tb);
   } else {
     auto k = hx_local_kernel<T, NP, NQ, false, VB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, VB * 64, smem);
+    if (e != cudaSuccess) return e;
+    const long long nblk = std::min<long long>(nitems, (long long)nsm * std::max(per_sm, 1));
     k<<<(unsigned)nblk, VB * 64, smem, s>>>(a, tb);
   }
   return cudaGetLastError();
