@@ -164,6 +164,44 @@ gbc_status gbc_cholgs(gbc_ctx* ctx, void* X, int nvec, int ldx, void* stream);
 gbc_status gbc_rayleigh_ritz(gbc_ctx* ctx, void* X, int nvec, int ldx, double* ritz,
                              void* stream);
 
+/* ---- batched systems (independent k-points / systems, Sec. III.B) ------------ */
+
+typedef struct gbc_batch gbc_batch;   /* opaque, owned by the library */
+
+/* Group ``nsys`` distinct contexts (same device and precision, each with its
+ * own mesh, fields, k-point and projectors) for batched filtering.  The batch
+ * borrows the contexts: destroy the batch before them. */
+gbc_status gbc_batch_create(gbc_batch** out, int nsys, gbc_ctx* const* systems);
+/* NULL-safe. */
+void gbc_batch_destroy(gbc_batch* batch);
+const char* gbc_batch_last_error(const gbc_batch* batch);
+
+/* gbc_filter on every system of the batch at once (Eq. chebfilt per system):
+ * X[i] is system i's block ([M_i][2][ldx[i]], the context precision), filtered
+ * in place to degree[i] with bounds[3i..3i+2] = (lT, lmax, lmin).  Systems that
+ * share the FE order, cell edges and k-point run their cell-level applies in
+ * one persistent launch (up to 8 per launch); the recurrence updates of all
+ * systems run in one launch per degree.  The whole degree loop is captured in a
+ * CUDA graph on the first call and replayed by later calls with the same
+ * arguments (pointers, sizes, degrees, bounds); other arguments re-capture.
+ * ``stream`` must be a created stream, not the legacy default stream (stream
+ * capture needs one).  Asynchronous. */
+gbc_status gbc_batch_filter(gbc_batch* batch, void* const* X, const int* nvec, const int* ldx,
+                            const int* degree, const double* bounds, void* stream);
+/* Kernels launched by one replay of the captured graph (0 before the first call). */
+gbc_status gbc_batch_launches(const gbc_batch* batch, int* kernels_per_call);
+
+/* ---- tile autotuner ------------------------------------------------------------ */
+
+/* Choose the FP32 cell-apply tile (1 or 2 vectors per CTA) for this context by
+ * timing both on a scratch block of ``nvec`` vectors (CUDA events); the choice
+ * is cached per (device, p, k != 0, nvec rounded up to a power of two) for the
+ * process and, when the environment variable GBC_TUNE_CACHE names a file,
+ * across processes.  Synchronous.  Uses the context's workspace. */
+gbc_status gbc_tune(gbc_ctx* ctx, int nvec, void* stream);
+/* Vectors per CTA the cell apply of this context uses. */
+gbc_status gbc_get_tile(const gbc_ctx* ctx, int* vectors_per_cta);
+
 /* ---- allocation-free variant ------------------------------------------------ */
 
 /* Y = H^k X exactly as gbc_apply_h computes it, for callers that cannot let the

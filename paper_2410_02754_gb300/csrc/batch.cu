@@ -1,0 +1,409 @@
+// Batched filters of many independent systems, the CUDA-graph replay of their
+// recurrence, and the tile autotuner.
+//
+// Paper: Sec. III.B (k-points -- and, by the same token, independent systems --
+// are mutually independent eigenproblems); each system runs the filter of
+// Eq. chebfilt.  Systems that share the FE order, cell edges and k-point share
+// the 1-D operator tables, so their cell-level applies run as one persistent
+// launch (up to GBC_MAX_BATCH systems per launch); the recurrence updates of
+// all active systems run as one launch.  The whole degree loop is captured
+// once in a CUDA graph and replayed while the call's arguments do not change.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gbc_internal.h"
+
+// ---------------------------------------------------------------------------
+// single-system cell apply with the context's tile
+// ---------------------------------------------------------------------------
+cudaError_t launch_hx_local_f64(const gbc_ctx* c, const double2* X, double2* Y, int nvec, int ldx,
+                                cudaStream_t s) {
+  HxJob j{c, X, Y, nvec, ldx};
+  return launch_hx_local_group_f64(&j, 1, 1, s);
+}
+
+cudaError_t launch_hx_local_f32(const gbc_ctx* c, const float2* X, float2* Y, int nvec, int ldx,
+                                cudaStream_t s) {
+  HxJob j{c, X, Y, nvec, ldx};
+  return launch_hx_local_group_f32(&j, 1, c->vb32, s);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: vectors per CTA of the FP32 cell apply
+// ---------------------------------------------------------------------------
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;   // key -> vb
+bool g_tune_loaded = false;
+
+std::string tune_file() {
+  const char* f = std::getenv("GBC_TUNE_CACHE");
+  return f ? std::string(f) : std::string();
+}
+
+// cache file: one "key vb" pair per line
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const std::string f = tune_file();
+  if (f.empty()) return;
+  FILE* fp = std::fopen(f.c_str(), "r");
+  if (!fp) return;
+  char key[512];
+  int vb = 0;
+  while (std::fscanf(fp, "%511s %d", key, &vb) == 2) g_tune_cache[key] = vb;
+  std::fclose(fp);
+}
+
+void tune_store() {
+  const std::string f = tune_file();
+  if (f.empty()) return;
+  FILE* fp = std::fopen(f.c_str(), "w");
+  if (!fp) return;
+  for (auto& kv : g_tune_cache) std::fprintf(fp, "%s %d\n", kv.first.c_str(), kv.second);
+  std::fclose(fp);
+}
+
+std::string tune_key(const gbc_ctx* c, int nvec) {
+  cudaDeviceProp prop;
+  std::string dev = "gpu";
+  if (cudaGetDeviceProperties(&prop, c->dev) == cudaSuccess) dev = prop.name;
+  for (auto& ch : dev)
+    if (ch == ' ') ch = '_';
+  const bool kpt = c->k[0] != 0.0 || c->k[1] != 0.0 || c->k[2] != 0.0;
+  int bucket = 1;
+  while (bucket < nvec) bucket <<= 1;
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "%s/fp32/p%d/k%d/nvec%d", dev.c_str(), c->mesh.p, kpt ? 1 : 0,
+                bucket);
+  return buf;
+}
+
+}  // namespace
+
+extern "C" gbc_status gbc_tune(gbc_ctx* c, int nvec, void* stream) {
+  if (!c) return GBC_EINVAL;
+  if (nvec < 1) return gbc_fail(c, GBC_EINVAL, "nvec >= 1 required");
+  GBC_TRY(gbc_prepare(c));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load();
+  const std::string key = tune_key(c, nvec);
+  auto it = g_tune_cache.find(key);
+  if (it != g_tune_cache.end()) {
+    c->vb32 = it->second;
+    return GBC_OK;
+  }
+  // time each candidate tile on a scratch block (work slots 0 and 1)
+  const size_t bytes = sizeof(float2) * 2 * (size_t)c->mesh.M * nvec;
+  GBC_TRY(gbc_ensure_work(c, 0, bytes));
+  GBC_TRY(gbc_ensure_work(c, 1, bytes));
+  float2* X = (float2*)c->work[1];
+  float2* Y = (float2*)c->work[0];
+  GBC_CU(c, cudaMemsetAsync(X, 0, bytes, s));
+  cudaEvent_t e0, e1;
+  GBC_CU(c, cudaEventCreate(&e0));
+  GBC_CU(c, cudaEventCreate(&e1));
+  const int cands[2] = {1, 2};
+  float best = 1e30f;
+  int best_vb = 2;
+  for (int vb : cands) {
+    HxJob j{c, X, Y, nvec, nvec};
+    float tot = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+      GBC_CU(c, cudaEventRecord(e0, s));
+      GBC_CU(c, launch_hx_local_group_f32(&j, 1, vb, s));
+      GBC_CU(c, cudaEventRecord(e1, s));
+      GBC_CU(c, cudaEventSynchronize(e1));
+      float ms = 0;
+      GBC_CU(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) tot += ms;   // first launch is a warm-up
+    }
+    if (tot < best) {
+      best = tot;
+      best_vb = vb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GBC_CU(c, cudaMemsetAsync(Y, 0, bytes, s));
+  c->vb32 = best_vb;
+  g_tune_cache[key] = best_vb;
+  tune_store();
+  return GBC_OK;
+}
+
+extern "C" gbc_status gbc_get_tile(const gbc_ctx* c, int* vectors_per_cta) {
+  if (!c || !vectors_per_cta) return GBC_EINVAL;
+  *vectors_per_cta = c->prec == GBC_FP64 ? 1 : c->vb32;
+  return GBC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched filter
+// ---------------------------------------------------------------------------
+struct gbc_batch {
+  std::vector<gbc_ctx*> sys;
+  std::string err;
+  int dev = 0;
+  gbc_precision prec = GBC_FP64;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<double> key;           // the arguments the cached graph was captured with
+  int launches = 0;                  // kernels in one replay
+};
+
+namespace {
+
+gbc_status bfail(gbc_batch* b, gbc_status st, const std::string& m) {
+  b->err = m;
+  return st;
+}
+
+void drop_graph(gbc_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->key.clear();
+}
+
+struct SysRun {
+  gbc_ctx* c;
+  void* X;
+  void* W;
+  void* Y;
+  int nvec, ldx, degree;
+  double cc, e;
+  std::vector<double> sig;
+};
+
+bool same_tables(const gbc_ctx* a, const gbc_ctx* b) {
+  if (a->mesh.p != b->mesh.p) return false;
+  for (int d = 0; d < 3; ++d)
+    if (a->h[d] != b->h[d] || a->k[d] != b->k[d]) return false;
+  return true;
+}
+
+// enqueue the whole degree loop of every system on stream s
+template <typename T>
+gbc_status record_filters(gbc_batch* b, std::vector<SysRun>& runs, cudaStream_t s, int* nlaunch) {
+  const size_t el = sizeof(cplx<T>);
+  int count = 0;
+  for (auto& r : runs) {
+    const size_t bytes = el * 2 * (size_t)r.c->mesh.M * r.ldx;
+    if (cudaMemsetAsync(r.Y, 0, bytes, s) != cudaSuccess) return bfail(b, GBC_ECUDA, "memset");
+  }
+  int maxdeg = 0;
+  for (auto& r : runs) maxdeg = std::max(maxdeg, r.degree);
+  for (int k = 0; k < maxdeg; ++k) {
+    std::vector<int> active;
+    for (int i = 0; i < (int)runs.size(); ++i)
+      if (runs[i].degree > k) active.push_back(i);
+    auto cur_of = [&](const SysRun& r) { return k == 0 ? r.X : ((k & 1) ? r.W : r.X); };
+    // cell-level applies: one launch per group of systems sharing the tables and tile
+    std::vector<bool> done(runs.size(), false);
+    for (size_t ai = 0; ai < active.size(); ++ai) {
+      const int i = active[ai];
+      if (done[i]) continue;
+      std::vector<HxJob> jobs;
+      for (size_t aj = ai; aj < active.size() && (int)jobs.size() < GBC_MAX_BATCH; ++aj) {
+        const int j = active[aj];
+        if (done[j] || !same_tables(runs[i].c, runs[j].c) || runs[i].c->vb32 != runs[j].c->vb32)
+          continue;
+        jobs.push_back(HxJob{runs[j].c, cur_of(runs[j]), runs[j].Y, runs[j].nvec, runs[j].ldx});
+        done[j] = true;
+      }
+      const cudaError_t e = std::is_same<T, double>::value
+                                ? launch_hx_local_group_f64(jobs.data(), (int)jobs.size(), 1, s)
+                                : launch_hx_local_group_f32(jobs.data(), (int)jobs.size(),
+                                                            runs[i].c->vb32, s);
+      if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("cell apply: ") + cudaGetErrorString(e));
+      ++count;
+    }
+    // nonlocal, per system
+    for (int i : active) {
+      SysRun& r = runs[i];
+      if (r.c->proj.natoms == 0) continue;
+      cplx<T>* C1 = (cplx<T>*)r.c->work[2];
+      cplx<T>* C2 = C1 + (size_t)r.c->proj.rows_total * r.nvec;
+      const cudaError_t e = launch_nonlocal<T>(r.c, (const cplx<T>*)cur_of(r), (cplx<T>*)r.Y,
+                                               r.nvec, r.ldx, C1, C2, s);
+      if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("nonlocal: ") + cudaGetErrorString(e));
+      count += 3;
+    }
+    // recurrence updates of all active systems, batched
+    for (size_t a0 = 0; a0 < active.size(); a0 += GBC_MAX_CHEB_BATCH) {
+      ChebBatch cb;
+      cb.njobs = 0;
+      cb.total = 0;
+      for (size_t ai = a0; ai < active.size() && cb.njobs < GBC_MAX_CHEB_BATCH; ++ai) {
+        SysRun& r = runs[active[ai]];
+        ChebJob& j = cb.job[cb.njobs++];
+        j.Y = r.Y;
+        j.invmd = std::is_same<T, double>::value ? (const void*)r.c->d_invmd
+                                                 : (const void*)r.c->d_invmd32;
+        j.nvec = r.nvec;
+        j.ldx = r.ldx;
+        j.c = r.cc;
+        j.start = cb.total;
+        if (k == 0) {
+          j.Xcur = r.X;
+          j.Xprev = nullptr;
+          j.Xout = r.W;
+          j.a = r.sig[0] / r.e;
+          j.b = 0.0;
+        } else {
+          void* cur = (k & 1) ? r.W : r.X;
+          void* prev = (k & 1) ? r.X : r.W;
+          j.Xcur = cur;
+          j.Xprev = prev;
+          j.Xout = prev;
+          j.a = 2.0 * r.sig[k] / r.e;
+          j.b = r.sig[k - 1] * r.sig[k];
+        }
+        cb.total += 2 * r.c->mesh.M * (long long)r.nvec;
+      }
+      const cudaError_t e = launch_cheb_batch<T>(cb, s);
+      if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("recurrence: ") + cudaGetErrorString(e));
+      ++count;
+    }
+  }
+  for (auto& r : runs) {
+    if (r.degree & 1) {
+      const cudaError_t e = launch_copy_block<T>((const cplx<T>*)r.W, (cplx<T>*)r.X, r.c->mesh.M,
+                                                 r.nvec, r.ldx, s);
+      if (e != cudaSuccess) return bfail(b, GBC_ECUDA, "final copy");
+      ++count;
+    }
+  }
+  *nlaunch = count;
+  return GBC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gbc_status gbc_batch_create(gbc_batch** out, int nsys, gbc_ctx* const* systems) {
+  if (!out) return GBC_EINVAL;
+  *out = nullptr;
+  if (nsys < 1 || nsys > 256 || !systems) return GBC_EINVAL;
+  for (int i = 0; i < nsys; ++i) {
+    if (!systems[i] || !systems[i]->mesh_set) return GBC_ESTATE;
+    if (systems[i]->dev != systems[0]->dev || systems[i]->prec != systems[0]->prec)
+      return GBC_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (systems[j] == systems[i]) return GBC_EINVAL;   // each context owns one system's workspaces
+  }
+  gbc_batch* b = new (std::nothrow) gbc_batch();
+  if (!b) return GBC_ENOMEM;
+  b->sys.assign(systems, systems + nsys);
+  b->dev = systems[0]->dev;
+  b->prec = systems[0]->prec;
+  *out = b;
+  return GBC_OK;
+}
+
+void gbc_batch_destroy(gbc_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->dev);
+  drop_graph(b);
+  delete b;
+}
+
+const char* gbc_batch_last_error(const gbc_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+gbc_status gbc_batch_filter(gbc_batch* b, void* const* X, const int* nvec, const int* ldx,
+                            const int* degree, const double* bounds, void* stream) {
+  if (!b) return GBC_EINVAL;
+  if (!X || !nvec || !ldx || !degree || !bounds) return bfail(b, GBC_EINVAL, "null argument");
+  const int n = (int)b->sys.size();
+  if (cudaSetDevice(b->dev) != cudaSuccess) return bfail(b, GBC_ECUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<SysRun> runs(n);
+  std::vector<double> key;
+  for (int i = 0; i < n; ++i) {
+    gbc_ctx* c = b->sys[i];
+    if (c->prec != b->prec) return bfail(b, GBC_ESTATE, "a system changed precision after gbc_batch_create");
+    const double lT = bounds[3 * i], lmax = bounds[3 * i + 1], lmin = bounds[3 * i + 2];
+    if (!X[i] || nvec[i] < 1 || ldx[i] < nvec[i] || degree[i] < 1)
+      return bfail(b, GBC_EINVAL, "system " + std::to_string(i) + ": bad block or degree");
+    if (!(lmin < lT && lT < lmax))
+      return bfail(b, GBC_EINVAL, "system " + std::to_string(i) + ": need lmin < lT < lmax");
+    if (gbc_prepare(c) != GBC_OK) return bfail(b, GBC_ESTATE, "system " + std::to_string(i) + ": " + c->err);
+    const size_t el = b->prec == GBC_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t bytes = el * 2 * (size_t)c->mesh.M * ldx[i];
+    // every workspace the graph touches is allocated before capture
+    if (gbc_ensure_work(c, 0, bytes) != GBC_OK || gbc_ensure_work(c, 1, bytes) != GBC_OK ||
+        gbc_ensure_work(c, 2, std::max<size_t>(64, 2 * el * (size_t)c->proj.rows_total * nvec[i])) != GBC_OK)
+      return bfail(b, GBC_ENOMEM, "system " + std::to_string(i) + ": " + c->err);
+    SysRun& r = runs[i];
+    r.c = c;
+    r.X = X[i];
+    r.Y = c->work[0];
+    r.W = c->work[1];
+    r.nvec = nvec[i];
+    r.ldx = ldx[i];
+    r.degree = degree[i];
+    r.cc = 0.5 * (lmax + lT);
+    r.e = 0.5 * (lmax - lT);
+    r.sig.resize(degree[i]);
+    r.sig[0] = r.e / (lmin - r.cc);
+    for (int k = 1; k < degree[i]; ++k) r.sig[k] = 1.0 / (2.0 / r.sig[0] - r.sig[k - 1]);
+    key.insert(key.end(), {(double)(uintptr_t)X[i], (double)nvec[i], (double)ldx[i],
+                           (double)degree[i], lT, lmax, lmin, (double)c->vb32,
+                           (double)(uintptr_t)c->work[0], (double)(uintptr_t)c->work[1],
+                           (double)(uintptr_t)c->work[2]});
+  }
+  if (b->exec && key == b->key) {
+    if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return bfail(b, GBC_ECUDA, "cudaGraphLaunch");
+    return GBC_OK;
+  }
+  drop_graph(b);
+  std::vector<bool> timing(n);
+  for (int i = 0; i < n; ++i) {
+    timing[i] = b->sys[i]->timing;
+    b->sys[i]->timing = false;
+  }
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    for (int i = 0; i < n; ++i) b->sys[i]->timing = timing[i];
+    return bfail(b, GBC_ECUDA, "cudaStreamBeginCapture (stream must not be the legacy default stream)");
+  }
+  int nl = 0;
+  gbc_status st = b->prec == GBC_FP64 ? record_filters<double>(b, runs, s, &nl)
+                                      : record_filters<float>(b, runs, s, &nl);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(s, &g);
+  for (int i = 0; i < n; ++i) b->sys[i]->timing = timing[i];
+  if (st != GBC_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return st != GBC_OK ? st : bfail(b, GBC_ECUDA, "cudaStreamEndCapture");
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    drop_graph(b);
+    return bfail(b, GBC_ECUDA, "cudaGraphInstantiate");
+  }
+  b->key = key;
+  b->launches = nl;
+  if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return bfail(b, GBC_ECUDA, "cudaGraphLaunch");
+  return GBC_OK;
+}
+
+gbc_status gbc_batch_launches(const gbc_batch* b, int* kernels_per_call) {
+  if (!b || !kernels_per_call) return GBC_EINVAL;
+  *kernels_per_call = b->launches;
+  return GBC_OK;
+}
+
+}  // extern "C"

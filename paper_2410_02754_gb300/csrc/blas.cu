@@ -38,6 +38,40 @@ __global__ void k_cheb_step(cplx<T>* __restrict__ Y, const cplx<T>* Xcur, const 
   }
 }
 
+// The same recurrence update for several systems in one launch (batched filter).
+template <typename T>
+__global__ void k_cheb_batch(const __grid_constant__ ChebBatch b) {
+  const long long n = b.total;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int q = 0;
+    for (int r = 1; r < b.njobs; ++r)
+      if (i >= b.job[r].start) q = r;
+    const ChebJob& j = b.job[q];
+    const long long li = i - j.start;
+    const long long r = li / j.nvec;
+    const int v = (int)(li - r * j.nvec);
+    const long long o = r * j.ldx + v;
+    cplx<T>* Y = (cplx<T>*)j.Y;
+    const cplx<T>* Xc = (const cplx<T>*)j.Xcur;
+    const cplx<T>* Xp = (const cplx<T>*)j.Xprev;
+    cplx<T>* Xo = (cplx<T>*)j.Xout;
+    const T w = ((const T*)j.invmd)[r >> 1];
+    const T a = (T)j.a, c = (T)j.c, bb = (T)j.b;
+    const cplx<T> y = Y[o], x = Xc[o];
+    cplx<T> out;
+    out.x = a * (w * y.x - c * x.x);
+    out.y = a * (w * y.y - c * x.y);
+    if (Xp) {
+      const cplx<T> xp = Xp[o];
+      out.x -= bb * xp.x;
+      out.y -= bb * xp.y;
+    }
+    Xo[o] = out;
+    Y[o] = cmake<cplx<T>>(0, 0);
+  }
+}
+
 // S[i][j] += sum_rows w(row) conj(X[row][i]) Y[row][j], FP64 accumulation.
 // Block: 32 x 32 tile of S, 256 threads with 2 x 2 outputs each; rows staged
 // 32 at a time; the grid's y dimension splits the rows into chunks.
@@ -331,6 +365,15 @@ cudaError_t launch_cheb_step(const cplx<T>* Y, const cplx<T>* Xcur, const cplx<T
                                                        (T)b);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_cheb_batch(const ChebBatch& b, cudaStream_t s) {
+  if (b.total <= 0) return cudaSuccess;
+  k_cheb_batch<T><<<grid_for(b.total), 256, 0, s>>>(b);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cheb_batch<float>(const ChebBatch&, cudaStream_t);
+template cudaError_t launch_cheb_batch<double>(const ChebBatch&, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_gram(const cplx<T>* X, const cplx<T>* Y, const double* md, long long M,

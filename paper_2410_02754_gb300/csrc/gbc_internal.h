@@ -11,6 +11,7 @@
 
 #define GBC_MAX_P 7
 #define GBC_MAX_NPJ 32
+#define GBC_MAX_BATCH 8     // systems per cell-apply launch
 
 // ---------------------------------------------------------------------------
 // complex helpers (float2 / double2 carry (re, im))
@@ -139,6 +140,7 @@ struct gbc_ctx {
   void* d_small = nullptr;           // small dense scratch (Gram, eigensolver)
   size_t small_bytes = 0;
   int* d_flag = nullptr;
+  int vb32 = 2;                      // FP32 cell-apply tile (vectors per CTA), set by the tuner
   // optional per-kernel-family timing (gbc_set_timing)
   bool timing = false;
   struct TimedLaunch { int family; cudaEvent_t a, b; };
@@ -179,7 +181,19 @@ gbc_status gbc_prepare(gbc_ctx* c);    // (re)builds fields / projector tables i
 // ---------------------------------------------------------------------------
 // launchers implemented in the .cu files
 // ---------------------------------------------------------------------------
-// hx_local_*.cu : Y += H^loc X (cell-level apply + atomic assembly)
+// hx_local_*.cu : Y += H^loc X (cell-level apply + atomic assembly), one launch
+// over up to GBC_MAX_BATCH systems sharing p, cell edges and k-point
+struct HxJob {
+  const gbc_ctx* c;
+  const void* X;
+  void* Y;
+  int nvec, ldx;
+};
+cudaError_t launch_hx_local_group_f64(const HxJob* jobs, int n, int vb, cudaStream_t s);
+cudaError_t launch_hx_local_group_f32(const HxJob* jobs, int n, int vb, cudaStream_t s);
+cudaError_t launch_hx_local_group_f32_vb1(const HxJob* jobs, int n, cudaStream_t s);
+cudaError_t launch_hx_local_group_f32_vb2(const HxJob* jobs, int n, cudaStream_t s);
+// single system, tile chosen by the context's tuned setting
 cudaError_t launch_hx_local_f64(const gbc_ctx* c, const double2* X, double2* Y, int nvec, int ldx,
                                 cudaStream_t s);
 cudaError_t launch_hx_local_f32(const gbc_ctx* c, const float2* X, float2* Y, int nvec, int ldx,
@@ -202,6 +216,25 @@ template <typename T>
 cudaError_t launch_cheb_step(const cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev,
                              cplx<T>* Xout, const T* invmd, long long M, int nvec, int ldx,
                              double a, double cshift, double b, cudaStream_t s);
+// batched recurrence update: one launch over several systems' blocks
+#define GBC_MAX_CHEB_BATCH 32
+struct ChebJob {
+  void* Y;
+  const void* Xcur;
+  const void* Xprev;   // may be null (first step)
+  void* Xout;
+  const void* invmd;   // float or double per the precision
+  long long start;     // first flat element (row * nvec + v) of this job
+  int nvec, ldx;
+  double a, c, b;
+};
+struct ChebBatch {
+  ChebJob job[GBC_MAX_CHEB_BATCH];
+  int njobs;
+  long long total;
+};
+template <typename T>
+cudaError_t launch_cheb_batch(const ChebBatch& b, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gram(const cplx<T>* X, const cplx<T>* Y, const double* md, long long M,
                         int nvec, int ldx, double2* S, cudaStream_t s);

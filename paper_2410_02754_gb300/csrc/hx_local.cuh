@@ -24,12 +24,22 @@
 
 namespace gbc {
 
-template <typename T> struct LocalArgs {
+// One system of a launch: its blocks, fields, mesh and the first global work item.
+template <typename T> struct SysDesc {
   const cplx<T>* X;
   cplx<T>* Y;
   const T* fields;   // [E][4][NQ^3]
-  int ldx, nvec;
+  int ldx, nvec, vchunks, pad;
+  long long item0;   // work items of this system: [item0, item0 + E * vchunks)
   MeshDev mesh;
+};
+
+// A launch covers up to GBC_MAX_BATCH systems that share p, the cell edges and
+// the k-point (hence the 1-D tables); items run over all systems.
+template <typename T> struct LocalArgs {
+  SysDesc<T> sys[GBC_MAX_BATCH];
+  int nsys;
+  long long nitems;
 };
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
@@ -50,7 +60,7 @@ template <int NQ> __device__ __forceinline__ int pidx(int x, int y, int z) {
 
 template <typename T, int NP, int NQ, bool KPT, int VB>
 __global__ void __launch_bounds__(VB * 64, sizeof(T) == 4 ? 3 : 2)
-hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
+hx_local_kernel(const __grid_constant__ LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
   using C = cplx<T>;
   constexpr int TPV = 64;
   constexpr int BUF = (NQ + 1) * (NQ + 1) * NQ;      // points per padded buffer
@@ -64,27 +74,35 @@ hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
 
   const int v = threadIdx.x % VB;
   const int lane = threadIdx.x / VB;
-  const int vchunks = (a.nvec + VB - 1) / VB;
-  const long long nitems = (long long)a.mesh.E * vchunks;
-  const int nx = a.mesh.ncell[0], ny = a.mesh.ncell[1];
+  const long long nitems = a.nitems;
+  auto locate = [&](long long it) {
+    int q = 0;
+#pragma unroll
+    for (int r = 1; r < GBC_MAX_BATCH; ++r)
+      if (r < a.nsys && it >= a.sys[r].item0) q = r;
+    return q;
+  };
 
   C* A = buf + v * VSTRIDE;
   C* Bb = A + BUF * 2;
   C* Cb = A + 2 * BUF * 2;
 
-  // Persistent CTA: items (cell, vector chunk), vector chunk fastest, taken with a
-  // grid stride so the CTAs running together work on neighbouring cells.  The next
-  // item's X^(e) and fields are loaded into registers while the current one is
-  // computed (the loads are issued right after the current item is staged).
+  // Persistent CTA: items (system, cell, vector chunk), vector chunk fastest, taken
+  // with a grid stride so the CTAs running together work on neighbouring cells.
+  // The next item's X^(e) and fields are loaded into registers while the current
+  // one is computed (the loads are issued right after the current item is staged).
   constexpr int PPL = (NP * NP * NP + TPV - 1) / TPV;       // nodes per lane
   constexpr int FPT = (4 * NQ3 + VB * TPV - 1) / (VB * TPV); // field values per thread
   C pfx[PPL][2];
   T pff[FPT];
   auto prefetch = [&](long long it) {
     if (it >= nitems) return;
-    const int e = (int)(it / vchunks);
-    const int vec = (int)(it % vchunks) * VB + v;
-    const bool vok = vec < a.nvec;
+    const SysDesc<T>& d = a.sys[locate(it)];
+    const long long li = it - d.item0;
+    const int e = (int)(li / d.vchunks);
+    const int vec = (int)(li % d.vchunks) * VB + v;
+    const bool vok = vec < d.nvec;
+    const int nx = d.mesh.ncell[0], ny = d.mesh.ncell[1];
     const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
 #pragma unroll
     for (int j = 0; j < PPL; ++j) {
@@ -92,14 +110,14 @@ hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
       pfx[j][0] = cmake<C>(0, 0);
       pfx[j][1] = cmake<C>(0, 0);
       if (i < NP * NP * NP && vok) {
-        const long long I = gbc_node(a.mesh, cx, cy, cz, i % NP, (i / NP) % NP, i / (NP * NP));
+        const long long I = gbc_node(d.mesh, cx, cy, cz, i % NP, (i / NP) % NP, i / (NP * NP));
         if (I >= 0) {
-          pfx[j][0] = a.X[(I * 2 + 0) * a.ldx + vec];
-          pfx[j][1] = a.X[(I * 2 + 1) * a.ldx + vec];
+          pfx[j][0] = d.X[(I * 2 + 0) * d.ldx + vec];
+          pfx[j][1] = d.X[(I * 2 + 1) * d.ldx + vec];
         }
       }
     }
-    const T* fsrc = a.fields + (size_t)e * 4 * NQ3;
+    const T* fsrc = d.fields + (size_t)e * 4 * NQ3;
 #pragma unroll
     for (int j = 0; j < FPT; ++j) {
       const int f = threadIdx.x + j * VB * TPV;
@@ -109,9 +127,12 @@ hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
   prefetch(blockIdx.x);
 
   for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
-  const int e = (int)(item / vchunks);
-  const int vec = (int)(item % vchunks) * VB + v;
-  const bool vok = vec < a.nvec;
+  const SysDesc<T>& d = a.sys[locate(item)];
+  const long long li = item - d.item0;
+  const int e = (int)(li / d.vchunks);
+  const int vec = (int)(li % d.vchunks) * VB + v;
+  const bool vok = vec < d.nvec;
+  const int nx = d.mesh.ncell[0], ny = d.mesh.ncell[1];
   const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
 
   // ---- stage X^(e) (both spins) and the cell's fields from the prefetch registers
@@ -368,10 +389,10 @@ hx_local_kernel(const LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
     if (vok) {
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        const long long I = gbc_node(a.mesh, cx, cy, cz, i, y, z);
+        const long long I = gbc_node(d.mesh, cx, cy, cz, i, y, z);
         if (I < 0) continue;
-        atomic_add_c<T>(&a.Y[(I * 2 + 0) * a.ldx + vec], yacc[k][0][i]);
-        atomic_add_c<T>(&a.Y[(I * 2 + 1) * a.ldx + vec], yacc[k][1][i]);
+        atomic_add_c<T>(&d.Y[(I * 2 + 0) * d.ldx + vec], yacc[k][0][i]);
+        atomic_add_c<T>(&d.Y[(I * 2 + 1) * d.ldx + vec], yacc[k][1][i]);
       }
     }
   }
@@ -402,45 +423,70 @@ inline Tables1D<T, NP, NQ> make_tables(const gbc_ctx* c) {
   return t;
 }
 
+// One launch over n systems that share p, the cell edges and the k-point; the
+// first system's context provides the 1-D tables.
 template <typename T, int NP, int VB>
-cudaError_t launch_hx_local_p(const gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx,
-                              cudaStream_t s) {
+cudaError_t launch_hx_group_p(const HxJob* jobs, int n, cudaStream_t s) {
   constexpr int NQ = NP + 1;   // nq = p + 2
+  if (n < 1 || n > GBC_MAX_BATCH) return cudaErrorInvalidValue;
   LocalArgs<T> a;
-  a.X = X;
-  a.Y = Y;
-  a.fields = std::is_same<T, double>::value ? (const T*)c->d_fields64 : (const T*)c->d_fields32;
-  a.ldx = ldx;
-  a.nvec = nvec;
-  a.mesh = c->mesh;
-  const auto tb = make_tables<T, NP, NQ>(c);
-  const bool kpt = (c->k[0] != 0.0 || c->k[1] != 0.0 || c->k[2] != 0.0);
+  long long item = 0;
+  for (int i = 0; i < GBC_MAX_BATCH; ++i) {
+    SysDesc<T>& d = a.sys[i];
+    if (i >= n) {
+      d = a.sys[0];
+      d.item0 = 0x7fffffffffffffffLL;
+      continue;
+    }
+    const gbc_ctx* c = jobs[i].c;
+    d.X = (const cplx<T>*)jobs[i].X;
+    d.Y = (cplx<T>*)jobs[i].Y;
+    d.fields = std::is_same<T, double>::value ? (const T*)c->d_fields64 : (const T*)c->d_fields32;
+    d.ldx = jobs[i].ldx;
+    d.nvec = jobs[i].nvec;
+    d.vchunks = (jobs[i].nvec + VB - 1) / VB;
+    d.pad = 0;
+    d.item0 = item;
+    d.mesh = c->mesh;
+    item += (long long)c->mesh.E * d.vchunks;
+  }
+  a.nsys = n;
+  a.nitems = item;
+  if (item <= 0) return cudaSuccess;
+  const gbc_ctx* c0 = jobs[0].c;
+  const auto tb = make_tables<T, NP, NQ>(c0);
+  const bool kpt = (c0->k[0] != 0.0 || c0->k[1] != 0.0 || c0->k[2] != 0.0);
   constexpr size_t smem = hx_local_smem<T, NP, NQ, VB>();
-  const long long nitems = (long long)c->mesh.E * ((nvec + VB - 1) / VB);
-  if (nitems <= 0) return cudaSuccess;
   int dev = 0, nsm = 0, per_sm = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (err != cudaSuccess) return err;
-  if (kpt) {
-    auto k = hx_local_kernel<T, NP, NQ, true, VB>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto run = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, VB * 64, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, VB * 64, smem);
     if (e != cudaSuccess) return e;
-    const long long nblk = std::min<long long>(nitems, (long long)nsm * std::max(per_sm, 1));
-    k<<<(unsigned)nblk, VB * 64, smem, s>>>(a, tb);
-  } else {
-    auto k = hx_local_kernel<T, NP, NQ, false, VB>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, VB * 64, smem);
-    if (e != cudaSuccess) return e;
-    const long long nblk = std::min<long long>(nitems, (long long)nsm * std::max(per_sm, 1));
-    k<<<(unsigned)nblk, VB * 64, smem, s>>>(a, tb);
+    const long long nblk = std::min<long long>(item, (long long)nsm * std::max(per_sm, 1));
+    kern<<<(unsigned)nblk, VB * 64, smem, s>>>(a, tb);
+    return cudaGetLastError();
+  };
+  if (kpt) return run(hx_local_kernel<T, NP, NQ, true, VB>);
+  return run(hx_local_kernel<T, NP, NQ, false, VB>);
+}
+
+// dispatch on p (nq = p + 2) for a fixed VB
+template <typename T, int VB>
+cudaError_t launch_hx_group(const HxJob* jobs, int n, cudaStream_t s) {
+  switch (jobs[0].c->mesh.p) {
+    case 2: return launch_hx_group_p<T, 3, VB>(jobs, n, s);
+    case 3: return launch_hx_group_p<T, 4, VB>(jobs, n, s);
+    case 4: return launch_hx_group_p<T, 5, VB>(jobs, n, s);
+    case 5: return launch_hx_group_p<T, 6, VB>(jobs, n, s);
+    case 6: return launch_hx_group_p<T, 7, VB>(jobs, n, s);
+    case 7: return launch_hx_group_p<T, 8, VB>(jobs, n, s);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace gbc

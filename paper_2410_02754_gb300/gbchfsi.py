@@ -27,7 +27,9 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_get_nnodes", "gbc_get_mass", "gbc_apply_h", "gbc_lanczos_bounds", "gbc_filter",
            "gbc_filter_residual",
            "gbc_cholgs", "gbc_rayleigh_ritz", "gbc_set_timing", "gbc_get_timing",
-           "gbc_apply_h_noalloc"]
+           "gbc_apply_h_noalloc", "gbc_batch_create", "gbc_batch_destroy",
+           "gbc_batch_last_error", "gbc_batch_filter", "gbc_batch_launches", "gbc_tune",
+           "gbc_get_tile"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -70,6 +72,13 @@ def load_library(path: str = LIB_PATH):
         "gbc_rayleigh_ritz": ([P, V, I, I, DP, V], I),
         "gbc_set_timing": ([P, I], I),
         "gbc_apply_h_noalloc": ([P, V, V, I, I, V], I),
+        "gbc_batch_create": ([ct.POINTER(P), I, ct.POINTER(P)], I),
+        "gbc_batch_destroy": ([P], None),
+        "gbc_batch_last_error": ([P], ct.c_char_p),
+        "gbc_batch_filter": ([P, ct.POINTER(P), IP, IP, IP, DP, V], I),
+        "gbc_batch_launches": ([P, IP], I),
+        "gbc_tune": ([P, I, V], I),
+        "gbc_get_tile": ([P, IP], I),
         "gbc_get_timing": ([P, I, DP, ct.POINTER(ct.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
@@ -260,3 +269,64 @@ class Context:
             self._chk(self.lib.gbc_get_timing(self.h, fam, ct.byref(t), ct.byref(n)))
             out[name] = (t.value, n.value)
         return out
+
+    # ---- tile autotuner -------------------------------------------------------------
+    def tune(self, nvec, stream=None):
+        """Pick the FP32 cell-apply tile by timing; returns vectors per CTA."""
+        self._chk(self.lib.gbc_tune(self.h, int(nvec), _stream_ptr(stream)))
+        return self.tile()
+
+    def tile(self):
+        v = ct.c_int()
+        self._chk(self.lib.gbc_get_tile(self.h, ct.byref(v)))
+        return v.value
+
+
+class Batch:
+    """Several contexts filtered together (one persistent cell-apply launch per
+    group of systems sharing FE order, cell edges and k-point; CUDA-graph replay)."""
+
+    def __init__(self, contexts):
+        self.lib = load_library()
+        self.ctxs = list(contexts)
+        arr = (ct.c_void_p * len(self.ctxs))(*[c.h for c in self.ctxs])
+        h = ct.c_void_p()
+        st = self.lib.gbc_batch_create(ct.byref(h), len(self.ctxs), arr)
+        if st != 0:
+            raise GbcError(st, "gbc_batch_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gbc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def filter(self, blocks, degrees, bounds, stream):
+        """blocks: tensors [M_i, 2, ldx_i]; degrees: ints; bounds: (lT, lmax, lmin) per
+        system; stream: a torch.cuda.Stream that is not the legacy default stream."""
+        n = len(self.ctxs)
+        ptrs, nv, ld = [], [], []
+        for c, X in zip(self.ctxs, blocks):
+            p, ldx = c._block(X)
+            ptrs.append(p.value)
+            nv.append(ldx)
+            ld.append(ldx)
+        Xa = (ct.c_void_p * n)(*ptrs)
+        a1, p1 = _iarr(nv)
+        a2, p2 = _iarr(ld)
+        a3, p3 = _iarr(degrees)
+        a4, p4 = _darr(np.asarray(bounds, np.float64).reshape(-1))
+        st = self.lib.gbc_batch_filter(self.h, Xa, p1, p2, p3, p4, _stream_ptr(stream))
+        if st != 0:
+            raise GbcError(st, self.lib.gbc_batch_last_error(self.h).decode())
+
+    def launches(self):
+        v = ct.c_int()
+        self.lib.gbc_batch_launches(self.h, ct.byref(v))
+        return v.value

@@ -352,3 +352,24 @@ def config(name: str, seed: int = 0, kindex: int = 0, **over) -> Problem:
     return make_problem(ncell=c["ncell"], h=h, p=c["p"], nq=c["nq"], periodic=(1, 1, 1),
                         k=ks[kindex], atom_pos=pos, natoms=natoms, channels=c["channels"],
                         seed=seed, name=name)
+
+
+def c2_systems(seed: int = 0):
+    """Sixteen independent periodic systems of uneven size for the batched filter:
+    8^3..14^3 cells, p in {4, 5, 6}, 64..320 vectors, 8..40 atoms with s, p, d
+    projectors (18 per atom), Chebyshev degree 12..24 (seed stream 6)."""
+    r = _rng(seed, 6)
+    out = []
+    for i in range(16):
+        n = int(r.integers(8, 15))
+        out.append(dict(ncell=(n, n, n), p=int(r.choice([4, 5, 6])), nvec=int(r.integers(64, 321)),
+                        natoms=int(r.integers(8, 41)), degree=int(r.integers(12, 25)),
+                        seed=seed * 1000 + i))
+    return out
+
+
+def c2_problem(desc) -> Problem:
+    """The Problem of one c2_systems() entry (Gamma point, 1 bohr cells)."""
+    return make_problem(ncell=desc["ncell"], h=(1.0, 1.0, 1.0), p=desc["p"], nq=desc["p"] + 2,
+                        periodic=(1, 1, 1), k=(0.0, 0.0, 0.0), natoms=desc["natoms"],
+                        channels=SPD_CHANNELS, seed=desc["seed"], name="c2")
