@@ -164,6 +164,36 @@ gbc_status gbc_cholgs(gbc_ctx* ctx, void* X, int nvec, int ldx, void* stream);
 gbc_status gbc_rayleigh_ritz(gbc_ctx* ctx, void* X, int nvec, int ldx, double* ritz,
                              void* stream);
 
+/* ---- backward (differentiation of the filter) -------------------------------- */
+
+/* Vector-Jacobian product of Y = gbc_filter(X0) (same degree and bounds) with
+ * respect to X0, V_eff, B_xc and Delta, for an upstream gradient GY = dL/dRe Y +
+ * i dL/dIm Y (device block, context precision).  Derived from Eq. chebfilt and
+ * Eqs. FEHloc / FEHnloc: the adjoint runs the same recurrence backwards,
+ * Lt_m = M_D^-1 GY, Lt_k = alpha_k L Lt_{k+1} - beta_{k+1} Lt_{k+2}, GX = M_D Lt_0,
+ * dL/dtheta = sum_k (alpha_k/e) Re(Lt_{k+1}^H dH/dtheta X_k).  X_k are
+ * checkpointed in pairs every ``ckpt_every`` degrees and recomputed.
+ * Outputs: GX (device block, written), gV and gB (host, E*nq^3 doubles each,
+ * gB = 3 consecutive arrays x, y, z, written; layout as gbc_set_fields),
+ * gDelta (host, the concatenated Delta matrices, complex128, Hermitian part,
+ * written; may be NULL).  p <= 6.  Synchronous.  Uses library workspace of
+ * (2 ceil(degree/ckpt_every) + max(ckpt_every, 3) + 4) blocks. */
+gbc_status gbc_filter_vjp(gbc_ctx* ctx, const void* X0, const void* GY, void* GX, double* gV,
+                          double* gB, double* gDelta, int nvec, int ldx, int degree, double lT,
+                          double lmax, double lmin, int ckpt_every, void* stream);
+
+/* L = sum_i w_i y_i^H H y_i for the block Y, with GY = 2 H Y diag(w) (device
+ * block, written) and the gradients of L at fixed Y with respect to V_eff, B_xc
+ * and Delta (host outputs as in gbc_filter_vjp).  w: host, nvec doubles.
+ * *loss: host.  p <= 6.  Synchronous. */
+gbc_status gbc_energy_grad(gbc_ctx* ctx, const void* Y, const double* w, void* GY, double* loss,
+                           double* gV, double* gB, double* gDelta, int nvec, int ldx,
+                           void* stream);
+
+/* Replace the atoms' Delta matrices (same count and sizes as the last
+ * gbc_set_projectors; layout as there).  Synchronous. */
+gbc_status gbc_set_delta(gbc_ctx* ctx, const double* delta);
+
 /* ---- batched systems (independent k-points / systems, Sec. III.B) ------------ */
 
 typedef struct gbc_batch gbc_batch;   /* opaque, owned by the library */

@@ -317,6 +317,15 @@ gbc_status promoted(gbc_ctx* c, float2* X, int nvec, int ldx, double* ritz, cuda
 
 }  // namespace
 
+// H.X in the context precision for the other translation units (Y zeroed
+// first when ``zero``)
+gbc_status gbc_apply_h_dev(gbc_ctx* c, const void* X, void* Y, int nvec, int ldx, bool zero,
+                           cudaStream_t s) {
+  if (c->prec == GBC_FP64)
+    return apply_h_t<double>(c, (const double2*)X, (double2*)Y, nvec, ldx, s, zero);
+  return apply_h_t<float>(c, (const float2*)X, (float2*)Y, nvec, ldx, s, zero);
+}
+
 // ---------------------------------------------------------------------------
 // public API
 // ---------------------------------------------------------------------------
@@ -353,7 +362,7 @@ void gbc_destroy(gbc_ctx* c) {
   for (auto e : c->event_pool) cudaEventDestroy(e);
   void* ptrs[] = {c->d_md, c->d_invmd, c->d_invmd32, c->d_rawfields, c->d_fields64, c->d_fields32,
                   c->work[0], c->work[1], c->work[2], c->work[3], c->work[4], c->work[5],
-                  c->work[6], c->work[7], c->d_small, c->d_flag};
+                  c->work[6], c->work[7], c->work[8], c->work[9], c->d_small, c->d_flag};
   for (void* p : ptrs) cudaFree(p);
   delete c;
 }

@@ -135,8 +135,12 @@ struct gbc_ctx {
   float* d_fields32 = nullptr;
   ProjDev proj;
   // workspaces
-  void* work[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t work_bytes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // 0 H.X accumulator, 1 second block, 2 nonlocal coefficients, 3 small dense,
+  // 4-7 FP64 copies / residual-split blocks, 8 backward block pool, 9 backward
+  // accumulators
+  void* work[10] = {nullptr, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t work_bytes[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   void* d_small = nullptr;           // small dense scratch (Gram, eigensolver)
   size_t small_bytes = 0;
   int* d_flag = nullptr;
@@ -177,6 +181,8 @@ gbc_status gbc_cuda_fail(gbc_ctx* c, cudaError_t e, const char* where);
 gbc_status gbc_ensure_work(gbc_ctx* c, int slot, size_t bytes);
 gbc_status gbc_ensure_small(gbc_ctx* c, size_t bytes);
 gbc_status gbc_prepare(gbc_ctx* c);    // (re)builds fields / projector tables if dirty
+gbc_status gbc_apply_h_dev(gbc_ctx* c, const void* X, void* Y, int nvec, int ldx, bool zero,
+                           cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // launchers implemented in the .cu files
@@ -202,6 +208,9 @@ cudaError_t launch_hx_local_f32(const gbc_ctx* c, const float2* X, float2* Y, in
 template <typename T>
 cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx,
                             cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_nl_project(gbc_ctx* c, const cplx<T>* X, int nvec, int ldx, cplx<T>* Cbuf,
+                              cudaStream_t s);
 // setup.cu
 gbc_status setup_tables(gbc_ctx* c);
 gbc_status setup_fields(gbc_ctx* c);
@@ -262,6 +271,13 @@ cudaError_t launch_convert_block(const double2* X, int ldx, float2* Out, int ldo
 template <typename T>
 cudaError_t launch_copy_block(const cplx<T>* X, cplx<T>* Out, long long M, int nvec, int ldx,
                               cudaStream_t s);
+// grad_contract.cu : quadrature-point gradient contraction (backward pass)
+cudaError_t launch_quad_grad_f64(const gbc_ctx* c, const double2* A, const double2* B,
+                                 const double* wv, double scale, int nvec, int ldx, double* g,
+                                 cudaStream_t s);
+cudaError_t launch_quad_grad_f32(const gbc_ctx* c, const float2* A, const float2* B,
+                                 const double* wv, double scale, int nvec, int ldx, double* g,
+                                 cudaStream_t s);
 // dense.cu : small dense FP64 linear algebra on the device
 gbc_status dense_cholesky_inv_h(gbc_ctx* c, double2* S, int n, double2* Q, cudaStream_t s);
 gbc_status dense_eigh(gbc_ctx* c, double2* A, int n, double* evals_dev, double2* Q,

@@ -110,3 +110,134 @@ __device__ __forceinline__ void interp_to_pencils(cplx<T>* P1, cplx<T>* P2, int 
   }
   __syncthreads();
 }
+
+template <typename T, int NP, int NQ, int VB>
+__global__ void __launch_bounds__(VB * 64)
+quad_grad_kernel(const GradArgs<T> a, const InterpTab<T, NP, NQ> tb) {
+  using C = cplx<T>;
+  constexpr int TPV = 64;
+  constexpr int BUF = (NQ + 1) * (NQ + 1) * NQ;
+  constexpr int VSTRIDE = 2 * BUF * 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int v = threadIdx.x % VB;
+  const int lane = threadIdx.x / VB;
+  const int e = blockIdx.x;
+  const int nx = a.mesh.ncell[0], ny = a.mesh.ncell[1];
+  const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
+  C* P1 = buf + v * VSTRIDE;
+  C* P2 = P1 + BUF * 2;
+  double acc[4][NQ];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[c][q] = 0.0;
+
+  for (int v0 = 0; v0 < a.nvec; v0 += VB) {
+    const int vec = v0 + v;
+    const bool vok = vec < a.nvec;
+    C ua[2][NQ], ub[2][NQ];
+#pragma unroll
+    for (int which = 0; which < 2; ++which) {
+      const cplx<T>* src = which == 0 ? a.A : a.B;
+      for (int i = lane; i < NP * NP * NP; i += TPV) {
+        const int ix = i % NP, iy = (i / NP) % NP, iz = i / (NP * NP);
+        const long long I = gbc_node(a.mesh, cx, cy, cz, ix, iy, iz);
+        C u = cmake<C>(0, 0), d = cmake<C>(0, 0);
+        if (I >= 0 && vok) {
+          u = src[(I * 2 + 0) * a.ldx + vec];
+          d = src[(I * 2 + 1) * a.ldx + vec];
+        }
+        const int q = gidx<NQ>(ix, iy, iz);
+        P1[2 * q] = u;
+        P1[2 * q + 1] = d;
+      }
+      __syncthreads();
+      if (which == 0)
+        interp_to_pencils<T, NP, NQ, TPV>(P1, P2, lane, tb, ua);
+      else
+        interp_to_pencils<T, NP, NQ, TPV>(P1, P2, lane, tb, ub);
+    }
+    if (lane < NQ * NQ && vok) {
+      const double w = a.wv ? a.wv[vec] : 1.0;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const C au = ua[0][q], ad = ua[1][q], bu = ub[0][q], bd = ub[1][q];
+        // Re(a^H b), Re(a^H sx b), Re(a^H sy b), Re(a^H sz b)
+        const T uu = au.x * bu.x + au.y * bu.y, dd = ad.x * bd.x + ad.y * bd.y;
+        const T ud_re = au.x * bd.x + au.y * bd.y, du_re = ad.x * bu.x + ad.y * bu.y;
+        const T ud_im = au.x * bd.y - au.y * bd.x, du_im = ad.x * bu.y - ad.y * bu.x;
+        acc[0][q] += w * (double)(uu + dd);
+        acc[1][q] += w * (double)(ud_re + du_re);
+        acc[2][q] += w * (double)(ud_im - du_im);
+        acc[3][q] += w * (double)(uu - dd);
+      }
+    }
+  }
+  // reduce over the VB threads that own the same pencil, then write g[e]
+  double* red = reinterpret_cast<double*>(smem_raw);   // [VB][64][4][NQ] overlays the buffers
+  __syncthreads();
+  if (lane < NQ * NQ) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) red[((v * 64 + lane) * 4 + c) * NQ + q] = acc[c][q];
+  }
+  __syncthreads();
+  if (v == 0 && lane < NQ * NQ) {
+    const int x = lane % NQ, y = lane / NQ;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int qz = 0; qz < NQ; ++qz) {
+        double sum = 0.0;
+        for (int w = 0; w < VB; ++w) sum += red[((w * 64 + lane) * 4 + c) * NQ + qz];
+        const int q = (qz * NQ + y) * NQ + x;
+        const double wq = tb.wq[x] * tb.wq[y] * tb.wq[qz] * tb.jac;
+        a.g[((size_t)e * 4 + c) * NQ * NQ * NQ + q] += a.scale * wq * sum;
+      }
+  }
+}
+
+template <typename T, int NP, int NQ, int VB> constexpr size_t quad_grad_smem() {
+  const size_t bufs = sizeof(cplx<T>) * (size_t)VB * (2 * ((NQ + 1) * (NQ + 1) * NQ) * 2 + 1);
+  const size_t red = sizeof(double) * (size_t)VB * 64 * 4 * NQ;
+  return bufs > red ? bufs : red;
+}
+
+template <typename T, int NP, int VB>
+cudaError_t launch_quad_grad_p(const gbc_ctx* c, const cplx<T>* A, const cplx<T>* B,
+                               const double* wv, double scale, int nvec, int ldx, double* g,
+                               cudaStream_t s) {
+  constexpr int NQ = NP + 1;
+  GradArgs<T> a{A, B, wv, g, ldx, nvec, scale, c->mesh};
+  InterpTab<T, NP, NQ> tb;
+  for (int i = 0; i < NP; ++i)
+    for (int q = 0; q < NQ; ++q) tb.N[i][q] = (T)c->tab.N1[i * NQ + q];
+  for (int q = 0; q < NQ; ++q) tb.wq[q] = c->tab.gq_w[q];
+  tb.jac = c->h[0] * c->h[1] * c->h[2] / 8.0;
+  constexpr size_t smem = quad_grad_smem<T, NP, NQ, VB>();
+  auto k = quad_grad_kernel<T, NP, NQ, VB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (c->mesh.E <= 0 || nvec <= 0) return cudaSuccess;
+  k<<<c->mesh.E, VB * 64, smem, s>>>(a, tb);
+  return cudaGetLastError();
+}
+
+template <typename T, int VB>
+cudaError_t launch_quad_grad_t(const gbc_ctx* c, const cplx<T>* A, const cplx<T>* B,
+                               const double* wv, double scale, int nvec, int ldx, double* g,
+                               cudaStream_t s) {
+  switch (c->mesh.p) {
+    case 2: return launch_quad_grad_p<T, 3, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
+    case 3: return launch_quad_grad_p<T, 4, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
+    case 4: return launch_quad_grad_p<T, 5, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
+    case 5: return launch_quad_grad_p<T, 6, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
+    case 6: return launch_quad_grad_p<T, 7, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
+    case 7: return launch_quad_grad_p<T, 8, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gbc

@@ -213,6 +213,24 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
   return cudaGetLastError();
 }
 
+// C = (P_a x I2)^H X for every atom (rows c_off + 2chi + s), C zeroed first
+template <typename T>
+cudaError_t launch_nl_project(gbc_ctx* c, const cplx<T>* X, int nvec, int ldx, cplx<T>* Cbuf,
+                              cudaStream_t s) {
+  const ProjDev& pj = c->proj;
+  if (pj.natoms == 0 || nvec == 0 || pj.nchunks == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(Cbuf, 0, sizeof(cplx<T>) * (size_t)pj.rows_total * nvec, s);
+  if (e != cudaSuccess) return e;
+  if (pj.max_npj <= 4) return run_project<T, 4>(c, X, nvec, ldx, Cbuf, s);
+  if (pj.max_npj <= 8) return run_project<T, 8>(c, X, nvec, ldx, Cbuf, s);
+  if (pj.max_npj <= 18) return run_project<T, 18>(c, X, nvec, ldx, Cbuf, s);
+  return run_project<T, GBC_MAX_NPJ>(c, X, nvec, ldx, Cbuf, s);
+}
+template cudaError_t launch_nl_project<float>(gbc_ctx*, const float2*, int, int, float2*,
+                                              cudaStream_t);
+template cudaError_t launch_nl_project<double>(gbc_ctx*, const double2*, int, int, double2*,
+                                               cudaStream_t);
+
 template cudaError_t launch_nonlocal<float>(gbc_ctx*, const float2*, float2*, int, int, float2*,
                                             float2*, cudaStream_t);
 template cudaError_t launch_nonlocal<double>(gbc_ctx*, const double2*, double2*, int, int,

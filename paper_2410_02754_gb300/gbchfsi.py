@@ -29,7 +29,7 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_cholgs", "gbc_rayleigh_ritz", "gbc_set_timing", "gbc_get_timing",
            "gbc_apply_h_noalloc", "gbc_batch_create", "gbc_batch_destroy",
            "gbc_batch_last_error", "gbc_batch_filter", "gbc_batch_launches", "gbc_tune",
-           "gbc_get_tile"]
+           "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -79,6 +79,9 @@ def load_library(path: str = LIB_PATH):
         "gbc_batch_launches": ([P, IP], I),
         "gbc_tune": ([P, I, V], I),
         "gbc_get_tile": ([P, IP], I),
+        "gbc_filter_vjp": ([P, V, V, V, DP, DP, DP, I, I, I, D, D, D, I, V], I),
+        "gbc_energy_grad": ([P, V, DP, V, DP, DP, DP, DP, I, I, V], I),
+        "gbc_set_delta": ([P, DP], I),
         "gbc_get_timing": ([P, I, DP, ct.POINTER(ct.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
@@ -144,6 +147,9 @@ class Context:
         n = ct.c_longlong()
         self._chk(self.lib.gbc_get_nnodes(self.h, ct.byref(n)))
         self.nnodes = n.value
+        self.ncells = int(np.prod(ncell))
+        self.nq = int(nq)
+        self.ndelta = 0
 
     def set_kpoint(self, k):
         kk, kp = _darr(k)
@@ -156,7 +162,9 @@ class Context:
     def set_projectors(self, natoms, npj, nsupp, supp_cell, supp_img, pvals, delta):
         if natoms == 0:
             self._chk(self.lib.gbc_set_projectors(self.h, 0, None, None, None, None, None, None))
+            self.ndelta = 0
             return
+        self.ndelta = int(sum(4 * int(n) * int(n) for n in npj))
         a1, p1 = _iarr(npj)
         a2, p2 = _iarr(nsupp)
         a3, p3 = _iarr(supp_cell)
@@ -269,6 +277,52 @@ class Context:
             self._chk(self.lib.gbc_get_timing(self.h, fam, ct.byref(t), ct.byref(n)))
             out[name] = (t.value, n.value)
         return out
+
+    # ---- backward ----------------------------------------------------------------
+    def _grad_outputs(self):
+        nq3 = self.nq ** 3
+        gV = np.zeros(self.ncells * nq3)
+        gB = np.zeros(3 * self.ncells * nq3)
+        gD = np.zeros(2 * self.ndelta)
+        return gV, gB, gD
+
+    def _split(self, gV, gB, gD):
+        n = self.ncells * self.nq ** 3
+        return (gV.reshape(self.ncells, -1), gB[:n].reshape(self.ncells, -1),
+                gB[n:2 * n].reshape(self.ncells, -1), gB[2 * n:].reshape(self.ncells, -1),
+                gD.view(np.complex128))
+
+    def filter_vjp(self, X0, GY, GX, degree, lT, lmax, lmin, ckpt_every=5, nvec=None, stream=None):
+        """Backward of filter: fills GX; returns (gV, gBx, gBy, gBz, gDelta)."""
+        px, ldx = self._block(X0)
+        pg, _ = self._block(GY)
+        po, _ = self._block(GX)
+        nvec = ldx if nvec is None else nvec
+        gV, gB, gD = self._grad_outputs()
+        dp = lambda a: a.ctypes.data_as(ct.POINTER(ct.c_double))
+        self._chk(self.lib.gbc_filter_vjp(self.h, px, pg, po, dp(gV), dp(gB), dp(gD), int(nvec),
+                                          int(ldx), int(degree), float(lT), float(lmax),
+                                          float(lmin), int(ckpt_every), _stream_ptr(stream)))
+        return self._split(gV, gB, gD)
+
+    def energy_grad(self, Y, w, GY, nvec=None, stream=None):
+        """L = sum_i w_i y_i^H H y_i; fills GY = 2 H Y diag(w); returns
+        (L, gV, gBx, gBy, gBz, gDelta) at fixed Y."""
+        py, ldx = self._block(Y)
+        pg, _ = self._block(GY)
+        nvec = ldx if nvec is None else nvec
+        ww, wp = _darr(np.asarray(w, np.float64)[:nvec])
+        gV, gB, gD = self._grad_outputs()
+        loss = ct.c_double()
+        dp = lambda a: a.ctypes.data_as(ct.POINTER(ct.c_double))
+        self._chk(self.lib.gbc_energy_grad(self.h, py, wp, pg, ct.byref(loss), dp(gV), dp(gB),
+                                           dp(gD), int(nvec), int(ldx), _stream_ptr(stream)))
+        return (loss.value,) + self._split(gV, gB, gD)
+
+    def set_delta(self, delta):
+        d = np.ascontiguousarray(delta, dtype=np.complex128)
+        a, p = _darr(d.view(np.float64))
+        self._chk(self.lib.gbc_set_delta(self.h, p))
 
     # ---- tile autotuner -------------------------------------------------------------
     def tune(self, nvec, stream=None):

@@ -1,0 +1,142 @@
+"""Backward of the filter on the GPU (gbc_filter_vjp, gbc_energy_grad and the
+torch.autograd wrappers) against the FP64 oracle gradients, and a central
+finite-difference check of the full-size config-1 mesh (FP64)."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import chfsi as oc
+from oracle import fe
+from oracle import grad as og
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+M_DEG, LT, LMAX, LMIN = 7, 2.0, 80.0, -2.5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def g():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2410_02754_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def small():
+    prob = syn.make_problem(ncell=(2, 2, 3), h=(1.2, 1.2, 1.2), p=3, k=(0.1, -0.2, 0.15), natoms=2,
+                            rc=1.2, seed=31, bmax=0.3, channels=((0.5, 0), (0.5, 1)))
+    d = fe.Discretisation(prob)
+    X0 = syn.random_block(d.mesh.nnodes, 3, 8)
+    w = np.random.default_rng(2).uniform(0, 1, 3)
+    Y = oc.cheb_filter(d.apply_htilde, X0, M_DEG, LT, LMAX, LMIN)
+    L, GY, gdir, gDdir = og.energy_and_direct_grads(d, Y, w)
+    gX, gf, gDf = og.filter_vjp(d, X0, GY, M_DEG, LT, LMAX, LMIN)
+    return prob, d, X0, w, Y, L, GY, gdir, gDdir, gX, gf, gDf
+
+
+@pytest.mark.parametrize("prec,tol,ck", [(0, 1e-10, 3), (0, 1e-10, 1), (1, 2e-4, 3)])
+def test_vjp_and_energy_match_oracle(g, small, prec, tol, ck):
+    prob, d, X0, w, Y, L, GY, gdir, gDdir, gX, gf, gDf = small
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    c = g.Context(0)
+    c.set_problem(prob)
+    c.set_precision(prec)
+    Yd = torch.from_numpy(Y).to(dt).cuda()
+    GYd = torch.empty_like(Yd)
+    Lg, gV, gBx, gBy, gBz, gD = c.energy_grad(Yd, w, GYd)
+    assert abs(Lg - L) < tol * abs(L)
+    assert rel(GYd.cpu().numpy(), GY) < tol
+    gg = np.stack([gV, gBx, gBy, gBz], 1)
+    assert rel(gg, gdir) < tol
+    nd = [x.size for x in gDdir]
+    assert rel(gD, np.concatenate([x.reshape(-1) for x in gDdir])) < tol
+    X0d = torch.from_numpy(X0).to(dt).cuda()
+    GYd = torch.from_numpy(GY).to(dt).cuda()
+    GXd = torch.empty_like(X0d)
+    gV, gBx, gBy, gBz, gD = c.filter_vjp(X0d, GYd, GXd, M_DEG, LT, LMAX, LMIN, ckpt_every=ck)
+    assert rel(GXd.cpu().numpy(), gX) < tol
+    assert rel(np.stack([gV, gBx, gBy, gBz], 1), gf) < tol
+    assert rel(gD, np.concatenate([x.reshape(-1) for x in gDf])) < tol
+    c.close()
+
+
+def test_autograd_end_to_end(g, small):
+    from paper_2410_02754_gb300.autograd import ChebFilterFn, EnergyFn
+    prob, d, X0, w, Y, L, GY, gdir, gDdir, gX, gf, gDf = small
+    c = g.Context(0)
+    c.set_problem(prob)
+    X = torch.from_numpy(X0).cuda().requires_grad_(True)
+    fields = [torch.from_numpy(np.array(a)).requires_grad_(True)
+              for a in (prob.veff, prob.bx, prob.by, prob.bz)]
+    delta = torch.from_numpy(np.concatenate([a.delta.reshape(-1) for a in prob.atoms])).requires_grad_(True)
+    Yt = ChebFilterFn.apply(X, *fields, delta, c, M_DEG, LT, LMAX, LMIN, 3)
+    Lt = EnergyFn.apply(Yt, *fields, delta, c, w)
+    Lt.backward()
+    assert abs(float(Lt.detach()) - L) < 1e-10 * abs(L)
+    assert rel(X.grad.cpu().numpy(), gX) < 1e-10
+    gtot = gdir + gf
+    for comp in range(4):
+        assert rel(fields[comp].grad.numpy(), gtot[:, comp]) < 1e-10
+    dtot = np.concatenate([(a + b).reshape(-1) for a, b in zip(gDdir, gDf)])
+    assert rel(delta.grad.numpy(), dtot) < 1e-10
+    c.close()
+
+
+def test_full_size_c1_mesh_gradients_vs_fd(g):
+    """Config-1 mesh, atoms and k-point, 4 vectors, degree 20, checkpoints every
+    5: the FP64 GPU gradient agrees with central differences of the FP64 GPU loss
+    along seeded directions, and the FP32 backward agrees with the FP64 one."""
+    prob = syn.config("c1", kindex=0)
+    c = g.Context(0)
+    c.set_problem(prob)
+    M = prob.nnodes
+    rng = np.random.default_rng(5)
+    X0 = syn.random_block(M, 4, 9)
+    w = rng.uniform(0, 1, 4)
+    lo, lmax = c.lanczos_bounds(torch.from_numpy(syn.random_start(M, 1)).cuda(), 10)
+    lmin, lT = min(lo, -1.0), lo + 5.0
+
+    def loss(veff=None, delta=None, X=None):
+        c.set_fields(prob.veff if veff is None else veff, prob.bx, prob.by, prob.bz)
+        if delta is not None:
+            c.set_delta(delta)
+        Xd = torch.from_numpy(X0 if X is None else X).cuda()
+        c.filter(Xd, 20, lT, lmax, lmin)
+        GY = torch.empty_like(Xd)
+        return c.energy_grad(Xd, w, GY)[0], Xd, GY
+
+    L, Yd, GYd = loss()
+    Lr, gV, gBx, gBy, gBz, gD = c.energy_grad(Yd, w, torch.empty_like(Yd))
+    X0d = torch.from_numpy(X0).cuda()
+    GX = torch.empty_like(X0d)
+    fV, fBx, fBy, fBz, fD = c.filter_vjp(X0d, GYd, GX, 20, lT, lmax, lmin, ckpt_every=5)
+    gVt, gDt = gV + fV, gD + fD
+    h = 1e-4
+    dV = rng.normal(size=prob.veff.shape)
+    num = (loss(veff=prob.veff + h * dV)[0] - loss(veff=prob.veff - h * dV)[0]) / (2 * h)
+    assert abs(num - np.sum(gVt * dV)) <= 1e-6 * abs(num)
+    D = rng.normal(size=X0.shape) + 1j * rng.normal(size=X0.shape)
+    num = (loss(X=X0 + h * D)[0] - loss(X=X0 - h * D)[0]) / (2 * h)
+    assert abs(num - np.real(np.sum(GX.cpu().numpy().conj() * D))) <= 1e-6 * abs(num)
+    delta0 = np.concatenate([a.delta.reshape(-1) for a in prob.atoms])
+    E = rng.normal(size=delta0.shape) + 1j * rng.normal(size=delta0.shape)
+    E = np.concatenate([0.5 * (B + B.conj().T).reshape(-1) for B in
+                        np.split(E, len(prob.atoms)) for B in [B.reshape(36, 36)]])
+    num = (loss(delta=delta0 + h * E)[0] - loss(delta=delta0 - h * E)[0]) / (2 * h)
+    c.set_delta(delta0)
+    assert abs(num - np.real(np.sum(gDt.conj() * E))) <= 1e-6 * abs(num)
+    # FP32 backward against the FP64 one
+    c.set_fields(prob.veff, prob.bx, prob.by, prob.bz)
+    c.set_precision(1)
+    GX32 = torch.empty(X0.shape, dtype=torch.complex64, device="cuda")
+    f32 = c.filter_vjp(X0d.to(torch.complex64), GYd.to(torch.complex64), GX32, 20, lT, lmax,
+                       lmin, ckpt_every=5)
+    assert rel(GX32.cpu().numpy(), GX.cpu().numpy()) < 1e-4
+    assert rel(f32[0], fV) < 1e-4
+    c.close()
