@@ -18,7 +18,9 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include "gbc_internal.h"
 
@@ -54,25 +56,161 @@ template <> __device__ __forceinline__ void atomic_add_c<double>(double2* p, dou
 }
 
 // point (x, y, z) -> index in a padded per-vector buffer
+// padded strides: y by NQ + 1, z by (NQ + 1) NQ + 1 points
 template <int NQ> __device__ __forceinline__ int pidx(int x, int y, int z) {
-  return x + y * (NQ + 1) + z * (NQ + 1) * (NQ + 1);
+  return x + y * (NQ + 1) + z * ((NQ + 1) * NQ + 1);
+}
+template <int NQ> __host__ __device__ constexpr int pbuf_points() {   // max pidx + 1
+  return (NQ - 1) * (1 + (NQ + 1) + ((NQ + 1) * NQ + 1)) + 1;
+}
+
+// ---------------------------------------------------------------------------
+// even-odd form of the 1-D operators
+//
+// GLL nodes and Gauss points are symmetric about the cell centre, so every 1-D
+// matrix used here is centro-symmetric (M[no-1-i][ni-1-j] = M[i][j]: mass,
+// stiffness, interpolation) or centro-antisymmetric (= -M[i][j]: C^ - C^T).
+// With e_j = x_j + x_{ni-1-j}, o_j = x_j - x_{ni-1-j} (j < ni/2) and the
+// middle entry x_mid when ni is odd,
+//   y_i          =      (E e)_i + (O o)_i + Mid_i x_mid
+//   y_{no-1-i}   = S * ((E e)_i - (O o)_i + Mid_i x_mid),   i < (no+1)/2,
+// E = (M_ij + M_i,ni-1-j)/2, O = (M_ij - M_i,ni-1-j)/2: about half the
+// multiply-adds of the dense product.
+// ---------------------------------------------------------------------------
+template <typename T, int NO, int NI> struct EO {
+  static constexpr int HO = (NO + 1) / 2;
+  static constexpr int HI = NI / 2 > 0 ? NI / 2 : 1;
+  T E[HO][HI];
+  T O[HO][HI];
+  T Mid[HO];
+};
+
+template <typename T, int NP, int NQ> struct TablesEO {
+  EO<T, NP, NP> B[3];    // 1-D Gauss mass h_d/2 B^               (symmetric)
+  EO<T, NP, NP> Gr[3];   // 1/2 A_d                                (symmetric)
+  EO<T, NP, NP> Gi[3];   // -1/2 k_d (C^ - C^T)                    (antisymmetric)
+  EO<T, NQ, NP> Ni;      // interpolation: y_q = sum_i l_i(xi_q) x_i (symmetric)
+  EO<T, NP, NQ> Nt;      // testing:       y_i = sum_q l_i(xi_q) x_q (symmetric)
+};
+
+template <int S, typename T, int NO, int NI, typename C>
+__device__ __forceinline__ void eo_apply(const EO<T, NO, NI>& M, const C (&x)[NI], C (&y)[NO]) {
+  constexpr int HI = NI / 2, HO = (NO + 1) / 2;
+  C e[HI > 0 ? HI : 1], o[HI > 0 ? HI : 1];
+#pragma unroll
+  for (int j = 0; j < HI; ++j) {
+    e[j].x = x[j].x + x[NI - 1 - j].x;
+    e[j].y = x[j].y + x[NI - 1 - j].y;
+    o[j].x = x[j].x - x[NI - 1 - j].x;
+    o[j].y = x[j].y - x[NI - 1 - j].y;
+  }
+#pragma unroll
+  for (int i = 0; i < HO; ++i) {
+    T er = 0, ei = 0, orr = 0, oi = 0;
+#pragma unroll
+    for (int j = 0; j < HI; ++j) {
+      er += M.E[i][j] * e[j].x;
+      ei += M.E[i][j] * e[j].y;
+      orr += M.O[i][j] * o[j].x;
+      oi += M.O[i][j] * o[j].y;
+    }
+    if (NI & 1) {
+      er += M.Mid[i] * x[HI].x;
+      ei += M.Mid[i] * x[HI].y;
+    }
+    y[i].x = er + orr;
+    y[i].y = ei + oi;
+    if (NO - 1 - i != i) {
+      y[NO - 1 - i].x = S * (er - orr);
+      y[NO - 1 - i].y = S * (ei - oi);
+    }
+  }
+}
+
+// complex operator Gr + i Gi (Gr symmetric, Gi antisymmetric) on complex data
+template <bool KPT, typename T, int N, typename C>
+__device__ __forceinline__ void g_apply(const EO<T, N, N>& Gr, const EO<T, N, N>& Gi,
+                                        const C (&x)[N], C (&y)[N]) {
+  eo_apply<1>(Gr, x, y);
+  if (KPT) {
+    C t[N];
+    eo_apply<-1>(Gi, x, t);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      y[i].x -= t[i].y;
+      y[i].y += t[i].x;
+    }
+  }
+}
+
+// host: even-odd split of a dense row-major NO x NI matrix (checks the symmetry)
+template <typename T, int NO, int NI>
+inline bool make_eo(const std::vector<double>& M, int S, EO<T, NO, NI>* out) {
+  double mx = 0;
+  for (double v : M) mx = std::max(mx, std::fabs(v));
+  for (int i = 0; i < NO; ++i)
+    for (int j = 0; j < NI; ++j)
+      if (std::fabs(M[i * NI + j] - S * M[(NO - 1 - i) * NI + (NI - 1 - j)]) > 1e-10 * (mx + 1e-300))
+        return false;
+  for (int i = 0; i < EO<T, NO, NI>::HO; ++i) {
+    for (int j = 0; j < EO<T, NO, NI>::HI; ++j) {
+      out->E[i][j] = (T)0;
+      out->O[i][j] = (T)0;
+      if (j < NI / 2) {
+        out->E[i][j] = (T)(0.5 * (M[i * NI + j] + M[i * NI + NI - 1 - j]));
+        out->O[i][j] = (T)(0.5 * (M[i * NI + j] - M[i * NI + NI - 1 - j]));
+      }
+    }
+    out->Mid[i] = (NI & 1) ? (T)M[i * NI + NI / 2] : (T)0;
+  }
+  return true;
+}
+
+template <typename T, int NP, int NQ>
+inline bool make_tables_eo(const gbc_ctx* c, TablesEO<T, NP, NQ>* t) {
+  const HostTables& h = c->tab;
+  bool ok = true;
+  for (int d = 0; d < 3; ++d) {
+    const double hd = c->h[d];
+    std::vector<double> B(NP * NP), Gr(NP * NP), Gi(NP * NP);
+    for (int i = 0; i < NP; ++i)
+      for (int j = 0; j < NP; ++j) {
+        B[i * NP + j] = 0.5 * hd * h.Bh[i * NP + j];
+        Gr[i * NP + j] = 0.5 * (2.0 / hd) * h.Ah[i * NP + j];
+        Gi[i * NP + j] = -0.5 * c->k[d] * (h.Ch[i * NP + j] - h.Ch[j * NP + i]);
+      }
+    ok = ok && make_eo<T, NP, NP>(B, 1, &t->B[d]) && make_eo<T, NP, NP>(Gr, 1, &t->Gr[d]) &&
+         make_eo<T, NP, NP>(Gi, -1, &t->Gi[d]);
+  }
+  std::vector<double> Ni(NQ * NP), Nt(NP * NQ);
+  for (int i = 0; i < NP; ++i)
+    for (int q = 0; q < NQ; ++q) {
+      Ni[q * NP + i] = h.N1[i * NQ + q];
+      Nt[i * NQ + q] = h.N1[i * NQ + q];
+    }
+  ok = ok && make_eo<T, NQ, NP>(Ni, 1, &t->Ni) && make_eo<T, NP, NQ>(Nt, 1, &t->Nt);
+  return ok;
 }
 
 template <typename T, int NP, int NQ, bool KPT, int VB>
-__global__ void __launch_bounds__(VB * 64, sizeof(T) == 4 ? 3 : 2)
-hx_local_kernel(const __grid_constant__ LocalArgs<T> a, const Tables1D<T, NP, NQ> tb) {
+__global__ void __launch_bounds__(VB * 64, sizeof(T) == 4 ? 4 : 2)
+hx_local_kernel(const __grid_constant__ LocalArgs<T> a, const TablesEO<T, NP, NQ> tb) {
   using C = cplx<T>;
   constexpr int TPV = 64;
-  constexpr int BUF = (NQ + 1) * (NQ + 1) * NQ;      // points per padded buffer
+  constexpr int NT = VB * TPV;
+  constexpr int BUF = pbuf_points<NQ>();             // points per padded buffer
   constexpr int NQ3 = NQ * NQ * NQ;
+  // per-vector stride = 8 (mod 16) complex: threads of neighbouring work units
+  // (vector fastest, then spin, then pencil) fall into distinct banks
+  constexpr int VBASE = 3 * BUF * 2;
+  constexpr int VSTRIDE = VBASE + ((24 - VBASE % 16) % 16);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // per-vector stride 3*BUF*2 + 1 complex: the 8-byte shift puts the vectors of a
-  // CTA (adjacent threads) in different shared-memory banks
-  constexpr int VSTRIDE = 3 * BUF * 2 + 1;
-  C* buf = reinterpret_cast<C*>(smem_raw);             // [VB][VSTRIDE]
-  T* fld = reinterpret_cast<T*>(buf + VB * VSTRIDE);   // [4][NQ3]
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  auto Ab = [&](int v) { return buf + v * VSTRIDE; };
+  auto Bb = [&](int v) { return buf + v * VSTRIDE + BUF * 2; };
+  auto Cb = [&](int v) { return buf + v * VSTRIDE + 2 * BUF * 2; };
 
-  const int v = threadIdx.x % VB;
+  const int v0 = threadIdx.x % VB;      // vector of this thread for gathering
   const int lane = threadIdx.x / VB;
   const long long nitems = a.nitems;
   auto locate = [&](long long it) {
@@ -83,348 +221,202 @@ hx_local_kernel(const __grid_constant__ LocalArgs<T> a, const Tables1D<T, NP, NQ
     return q;
   };
 
-  C* A = buf + v * VSTRIDE;
-  C* Bb = A + BUF * 2;
-  C* Cb = A + 2 * BUF * 2;
-
-  // Persistent CTA: items (system, cell, vector chunk), vector chunk fastest, taken
-  // with a grid stride so the CTAs running together work on neighbouring cells.
-  // The next item's X^(e) and fields are loaded into registers while the current
-  // one is computed (the loads are issued right after the current item is staged).
-  constexpr int PPL = (NP * NP * NP + TPV - 1) / TPV;       // nodes per lane
-  constexpr int FPT = (4 * NQ3 + VB * TPV - 1) / (VB * TPV); // field values per thread
-  C pfx[PPL][2];
-  T pff[FPT];
-  auto prefetch = [&](long long it) {
-    if (it >= nitems) return;
-    const SysDesc<T>& d = a.sys[locate(it)];
-    const long long li = it - d.item0;
-    const int e = (int)(li / d.vchunks);
-    const int vec = (int)(li % d.vchunks) * VB + v;
-    const bool vok = vec < d.nvec;
-    const int nx = d.mesh.ncell[0], ny = d.mesh.ncell[1];
-    const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
-#pragma unroll
-    for (int j = 0; j < PPL; ++j) {
-      const int i = lane + j * TPV;
-      pfx[j][0] = cmake<C>(0, 0);
-      pfx[j][1] = cmake<C>(0, 0);
-      if (i < NP * NP * NP && vok) {
-        const long long I = gbc_node(d.mesh, cx, cy, cz, i % NP, (i / NP) % NP, i / (NP * NP));
-        if (I >= 0) {
-          pfx[j][0] = d.X[(I * 2 + 0) * d.ldx + vec];
-          pfx[j][1] = d.X[(I * 2 + 1) * d.ldx + vec];
-        }
-      }
-    }
-    const T* fsrc = d.fields + (size_t)e * 4 * NQ3;
-#pragma unroll
-    for (int j = 0; j < FPT; ++j) {
-      const int f = threadIdx.x + j * VB * TPV;
-      pff[j] = f < 4 * NQ3 ? fsrc[f] : (T)0;
-    }
-  };
-  prefetch(blockIdx.x);
+  // work units of the single-spin stages: u -> (vector, spin, pencil), vector fastest
+  constexpr int XU = VB * NP * NP * 2;          // units of the x-pencil stages
+  constexpr int XR = (XU + NT - 1) / NT;        // rounds per thread
 
   for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
-  const SysDesc<T>& d = a.sys[locate(item)];
-  const long long li = item - d.item0;
-  const int e = (int)(li / d.vchunks);
-  const int vec = (int)(li % d.vchunks) * VB + v;
-  const bool vok = vec < d.nvec;
-  const int nx = d.mesh.ncell[0], ny = d.mesh.ncell[1];
-  const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
+    const SysDesc<T>& d = a.sys[locate(item)];
+    const long long li = item - d.item0;
+    const int e = (int)(li / d.vchunks);
+    const int vbase = (int)(li % d.vchunks) * VB;
+    const int nx = d.mesh.ncell[0], ny = d.mesh.ncell[1];
+    const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
 
-  // ---- stage X^(e) (both spins) and the cell's fields from the prefetch registers
-#pragma unroll
-  for (int j = 0; j < PPL; ++j) {
-    const int i = lane + j * TPV;
-    if (i < NP * NP * NP) {
-      const int q = pidx<NQ>(i % NP, (i / NP) % NP, i / (NP * NP));
-      A[2 * q] = pfx[j][0];
-      A[2 * q + 1] = pfx[j][1];
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < FPT; ++j) {
-    const int f = threadIdx.x + j * VB * TPV;
-    if (f < 4 * NQ3) fld[f] = pff[j];
-  }
-  __syncthreads();
-  prefetch(item + gridDim.x);
-
-  // ===== kinetic / k part:  Y = G_x(B_y B_z X) + B_x(G_y B_z X + B_y G_z X)
-  // z-stage: T1 = B_z X -> Bb, T2 = G_z X -> Cb
-  for (int pid = lane; pid < NP * NP; pid += TPV) {
-    const int x = pid % NP, y = pid / NP;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C in[NP];
-#pragma unroll
-      for (int j = 0; j < NP; ++j) in[j] = A[2 * pidx<NQ>(x, y, j) + s];
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T t1r = 0, t1i = 0, t2r = 0, t2i = 0;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          t1r += tb.B[2][i][j] * in[j].x;
-          t1i += tb.B[2][i][j] * in[j].y;
-          t2r += tb.Gr[2][i][j] * in[j].x;
-          t2i += tb.Gr[2][i][j] * in[j].y;
-          if (KPT) {
-            t2r -= tb.Gi[2][i][j] * in[j].y;
-            t2i += tb.Gi[2][i][j] * in[j].x;
-          }
+    // ---- extract X^(e) (both spins) into A
+    {
+      const int vec = vbase + v0;
+      const bool vok = vec < d.nvec;
+      for (int i = lane; i < NP * NP * NP; i += TPV) {
+        const int ix = i % NP, iy = (i / NP) % NP, iz = i / (NP * NP);
+        const long long I = gbc_node(d.mesh, cx, cy, cz, ix, iy, iz);
+        C u = cmake<C>(0, 0), dn = cmake<C>(0, 0);
+        if (I >= 0 && vok) {
+          u = d.X[(I * 2 + 0) * d.ldx + vec];
+          dn = d.X[(I * 2 + 1) * d.ldx + vec];
         }
-        Bb[2 * pidx<NQ>(x, y, i) + s] = cmake<C>(t1r, t1i);
-        Cb[2 * pidx<NQ>(x, y, i) + s] = cmake<C>(t2r, t2i);
+        const int q = pidx<NQ>(ix, iy, iz);
+        Ab(v0)[2 * q] = u;
+        Ab(v0)[2 * q + 1] = dn;
       }
     }
-  }
-  __syncthreads();
-  // y-stage (in place): U1 = B_y T1 -> Bb, U2 = G_y T1 + B_y T2 -> Cb
-  for (int pid = lane; pid < NP * NP; pid += TPV) {
-    const int x = pid % NP, z = pid / NP;
+    const T* __restrict__ fld = d.fields + (size_t)e * 4 * NQ3;   // read through L1
+    __syncthreads();
+
+    // ===== kinetic / k part: Y = G_x(B_y B_z X) + B_x(G_y B_z X + B_y G_z X)
+    // z-stage: T1 = B_z X -> Bb, T2 = G_z X -> Cb
+    for (int u = threadIdx.x; u < VB * NP * NP * 2; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int x = pen % NP, y = pen / NP;
+      C in[NP], t1[NP], t2[NP];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C t1[NP], t2[NP];
+      for (int j = 0; j < NP; ++j) in[j] = Ab(v)[2 * pidx<NQ>(x, y, j) + s];
+      eo_apply<1>(tb.B[2], in, t1);
+      g_apply<KPT>(tb.Gr[2], tb.Gi[2], in, t2);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        Bb(v)[2 * pidx<NQ>(x, y, i) + s] = t1[i];
+        Cb(v)[2 * pidx<NQ>(x, y, i) + s] = t2[i];
+      }
+    }
+    __syncthreads();
+    // y-stage (in place): U1 = B_y T1 -> Bb, U2 = G_y T1 + B_y T2 -> Cb
+    for (int u = threadIdx.x; u < VB * NP * NP * 2; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int x = pen % NP, z = pen / NP;
+      C t1[NP], t2[NP], u1[NP], u2[NP], w2[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
-        t1[j] = Bb[2 * pidx<NQ>(x, j, z) + s];
-        t2[j] = Cb[2 * pidx<NQ>(x, j, z) + s];
+        t1[j] = Bb(v)[2 * pidx<NQ>(x, j, z) + s];
+        t2[j] = Cb(v)[2 * pidx<NQ>(x, j, z) + s];
       }
+      eo_apply<1>(tb.B[1], t1, u1);
+      g_apply<KPT>(tb.Gr[1], tb.Gi[1], t1, u2);
+      eo_apply<1>(tb.B[1], t2, w2);
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        T u1r = 0, u1i = 0, u2r = 0, u2i = 0;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          u1r += tb.B[1][i][j] * t1[j].x;
-          u1i += tb.B[1][i][j] * t1[j].y;
-          u2r += tb.Gr[1][i][j] * t1[j].x + tb.B[1][i][j] * t2[j].x;
-          u2i += tb.Gr[1][i][j] * t1[j].y + tb.B[1][i][j] * t2[j].y;
-          if (KPT) {
-            u2r -= tb.Gi[1][i][j] * t1[j].y;
-            u2i += tb.Gi[1][i][j] * t1[j].x;
-          }
-        }
-        Bb[2 * pidx<NQ>(x, i, z) + s] = cmake<C>(u1r, u1i);
-        Cb[2 * pidx<NQ>(x, i, z) + s] = cmake<C>(u2r, u2i);
+        Bb(v)[2 * pidx<NQ>(x, i, z) + s] = u1[i];
+        Cb(v)[2 * pidx<NQ>(x, i, z) + s] = cadd(u2[i], w2[i]);
       }
     }
-  }
-  __syncthreads();
-  // x-stage: Y = G_x U1 + B_x U2, kept in registers (one x-pencil per lane)
-  constexpr int NPEN = (NP * NP + TPV - 1) / TPV;    // x-pencils per lane (1 for p <= 7)
-  C yacc[NPEN][2][NP];
+    __syncthreads();
+    // x-stage: Y = G_x U1 + B_x U2, kept in registers per work unit
+    C yacc[XR][NP];
 #pragma unroll
-  for (int k = 0; k < NPEN; ++k) {
-    const int pid = lane + k * TPV;
-    if (pid >= NP * NP) break;
-    const int y = pid % NP, z = pid / NP;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C u1[NP], u2[NP];
+    for (int r = 0; r < XR; ++r) {
+      const int u = threadIdx.x + r * NT;
+      if (u >= XU) break;
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int y = pen % NP, z = pen / NP;
+      C u1[NP], u2[NP], w2[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
-        u1[j] = Bb[2 * pidx<NQ>(j, y, z) + s];
-        u2[j] = Cb[2 * pidx<NQ>(j, y, z) + s];
+        u1[j] = Bb(v)[2 * pidx<NQ>(j, y, z) + s];
+        u2[j] = Cb(v)[2 * pidx<NQ>(j, y, z) + s];
       }
+      g_apply<KPT>(tb.Gr[0], tb.Gi[0], u1, yacc[r]);
+      eo_apply<1>(tb.B[0], u2, w2);
 #pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T yr = 0, yi = 0;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          yr += tb.Gr[0][i][j] * u1[j].x + tb.B[0][i][j] * u2[j].x;
-          yi += tb.Gr[0][i][j] * u1[j].y + tb.B[0][i][j] * u2[j].y;
-          if (KPT) {
-            yr -= tb.Gi[0][i][j] * u1[j].y;
-            yi += tb.Gi[0][i][j] * u1[j].x;
-          }
-        }
-        yacc[k][s][i] = cmake<C>(yr, yi);
-      }
+      for (int i = 0; i < NP; ++i) yacc[r][i] = cadd(yacc[r][i], w2[i]);
     }
-  }
-  __syncthreads();
+    __syncthreads();
 
-  // ===== V_eff / B_xc part through the Gauss points
-  // interp x: A (np,np,np) -> Bb (nq,np,np)
-  for (int pid = lane; pid < NP * NP; pid += TPV) {
-    const int y = pid % NP, z = pid / NP;
+    // ===== V_eff / B_xc part through the Gauss points
+    // interp x: A (np,np,np) -> Bb (nq,np,np)
+    for (int u = threadIdx.x; u < VB * NP * NP * 2; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int y = pen % NP, z = pen / NP;
+      C in[NP], out[NQ];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C in[NP];
+      for (int j = 0; j < NP; ++j) in[j] = Ab(v)[2 * pidx<NQ>(j, y, z) + s];
+      eo_apply<1>(tb.Ni, in, out);
 #pragma unroll
-      for (int j = 0; j < NP; ++j) in[j] = A[2 * pidx<NQ>(j, y, z) + s];
+      for (int q = 0; q < NQ; ++q) Bb(v)[2 * pidx<NQ>(q, y, z) + s] = out[q];
+    }
+    __syncthreads();
+    // interp y: Bb (nq,np,np) -> Cb (nq,nq,np)
+    for (int u = threadIdx.x; u < VB * NQ * NP * 2; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int x = pen % NQ, z = pen / NQ;
+      C in[NP], out[NQ];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) in[j] = Bb(v)[2 * pidx<NQ>(x, j, z) + s];
+      eo_apply<1>(tb.Ni, in, out);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) Cb(v)[2 * pidx<NQ>(x, q, z) + s] = out[q];
+    }
+    __syncthreads();
+    // interp z + pointwise spin operator: Cb (nq,nq,np) -> Bb (nq,nq,nq), both spins
+    for (int u = threadIdx.x; u < VB * NQ * NQ; u += NT) {
+      const int v = u % VB, pen = u / VB;
+      const int x = pen % NQ, y = pen / NQ;
+      C iu[NP], id[NP], ou[NQ], od[NQ];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        iu[j] = Cb(v)[2 * pidx<NQ>(x, y, j)];
+        id[j] = Cb(v)[2 * pidx<NQ>(x, y, j) + 1];
+      }
+      eo_apply<1>(tb.Ni, iu, ou);
+      eo_apply<1>(tb.Ni, id, od);
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
-        T r = 0, im = 0;
+        const int qq = (q * NQ + y) * NQ + x;
+        const T V = __ldg(fld + qq), bx = __ldg(fld + NQ3 + qq), by = __ldg(fld + 2 * NQ3 + qq),
+                bz = __ldg(fld + 3 * NQ3 + qq);
+        const T ur = ou[q].x, ui = ou[q].y, dr = od[q].x, di = od[q].y;
+        // [(V + bz) u + (bx - i by) d ; (bx + i by) u + (V - bz) d]
+        Bb(v)[2 * pidx<NQ>(x, y, q)] =
+            cmake<C>((V + bz) * ur + bx * dr + by * di, (V + bz) * ui + bx * di - by * dr);
+        Bb(v)[2 * pidx<NQ>(x, y, q) + 1] =
+            cmake<C>(bx * ur - by * ui + (V - bz) * dr, bx * ui + by * ur + (V - bz) * di);
+      }
+    }
+    __syncthreads();
+    // test z: Bb (nq,nq,nq) -> Cb (nq,nq,np)
+    for (int u = threadIdx.x; u < VB * NQ * NQ * 2; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int x = pen % NQ, y = pen / NQ;
+      C in[NQ], out[NP];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          r += tb.N[j][q] * in[j].x;
-          im += tb.N[j][q] * in[j].y;
+      for (int q = 0; q < NQ; ++q) in[q] = Bb(v)[2 * pidx<NQ>(x, y, q) + s];
+      eo_apply<1>(tb.Nt, in, out);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) Cb(v)[2 * pidx<NQ>(x, y, i) + s] = out[i];
+    }
+    __syncthreads();
+    // test y: Cb (nq,nq,np) -> Bb (nq,np,np)
+    for (int u = threadIdx.x; u < VB * NQ * NP * 2; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int x = pen % NQ, z = pen / NQ;
+      C in[NQ], out[NP];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) in[q] = Cb(v)[2 * pidx<NQ>(x, q, z) + s];
+      eo_apply<1>(tb.Nt, in, out);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) Bb(v)[2 * pidx<NQ>(x, i, z) + s] = out[i];
+    }
+    __syncthreads();
+    // test x: Bb (nq,np,np) -> add into the x-stage registers, then assemble
+#pragma unroll
+    for (int r = 0; r < XR; ++r) {
+      const int u = threadIdx.x + r * NT;
+      if (u >= XU) break;
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int y = pen % NP, z = pen / NP;
+      C in[NQ], out[NP];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) in[q] = Bb(v)[2 * pidx<NQ>(q, y, z) + s];
+      eo_apply<1>(tb.Nt, in, out);
+      const int vec = vbase + v;
+      if (vec < d.nvec) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const long long I = gbc_node(d.mesh, cx, cy, cz, i, y, z);
+          if (I < 0) continue;
+          atomic_add_c<T>(&d.Y[(I * 2 + s) * d.ldx + vec], cadd(yacc[r][i], out[i]));
         }
-        Bb[2 * pidx<NQ>(q, y, z) + s] = cmake<C>(r, im);
       }
     }
-  }
-  __syncthreads();
-  // interp y: Bb (nq,np,np) -> Cb (nq,nq,np)
-  for (int pid = lane; pid < NQ * NP; pid += TPV) {
-    const int x = pid % NQ, z = pid / NQ;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C in[NP];
-#pragma unroll
-      for (int j = 0; j < NP; ++j) in[j] = Bb[2 * pidx<NQ>(x, j, z) + s];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        T r = 0, im = 0;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          r += tb.N[j][q] * in[j].x;
-          im += tb.N[j][q] * in[j].y;
-        }
-        Cb[2 * pidx<NQ>(x, q, z) + s] = cmake<C>(r, im);
-      }
-    }
-  }
-  __syncthreads();
-  // interp z + pointwise spin operator: Cb (nq,nq,np) -> Bb (nq,nq,nq)
-  for (int pid = lane; pid < NQ * NQ; pid += TPV) {
-    const int x = pid % NQ, y = pid / NQ;
-    C iu[NP], id[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      iu[j] = Cb[2 * pidx<NQ>(x, y, j)];
-      id[j] = Cb[2 * pidx<NQ>(x, y, j) + 1];
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      T ur = 0, ui = 0, dr = 0, di = 0;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        ur += tb.N[j][q] * iu[j].x;
-        ui += tb.N[j][q] * iu[j].y;
-        dr += tb.N[j][q] * id[j].x;
-        di += tb.N[j][q] * id[j].y;
-      }
-      const int qq = (q * NQ + y) * NQ + x;
-      const T V = fld[qq], bx = fld[NQ3 + qq], by = fld[2 * NQ3 + qq], bz = fld[3 * NQ3 + qq];
-      // [(V + bz) u + (bx - i by) d ; (bx + i by) u + (V - bz) d]
-      const T our = (V + bz) * ur + bx * dr + by * di;
-      const T oui = (V + bz) * ui + bx * di - by * dr;
-      const T odr = bx * ur - by * ui + (V - bz) * dr;
-      const T odi = bx * ui + by * ur + (V - bz) * di;
-      Bb[2 * pidx<NQ>(x, y, q)] = cmake<C>(our, oui);
-      Bb[2 * pidx<NQ>(x, y, q) + 1] = cmake<C>(odr, odi);
-    }
-  }
-  __syncthreads();
-  // test z: Bb (nq,nq,nq) -> Cb (nq,nq,np)
-  for (int pid = lane; pid < NQ * NQ; pid += TPV) {
-    const int x = pid % NQ, y = pid / NQ;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C in[NQ];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) in[q] = Bb[2 * pidx<NQ>(x, y, q) + s];
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T r = 0, im = 0;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          r += tb.N[i][q] * in[q].x;
-          im += tb.N[i][q] * in[q].y;
-        }
-        Cb[2 * pidx<NQ>(x, y, i) + s] = cmake<C>(r, im);
-      }
-    }
-  }
-  __syncthreads();
-  // test y: Cb (nq,nq,np) -> Bb (nq,np,np)
-  for (int pid = lane; pid < NQ * NP; pid += TPV) {
-    const int x = pid % NQ, z = pid / NQ;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C in[NQ];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) in[q] = Cb[2 * pidx<NQ>(x, q, z) + s];
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T r = 0, im = 0;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          r += tb.N[i][q] * in[q].x;
-          im += tb.N[i][q] * in[q].y;
-        }
-        Bb[2 * pidx<NQ>(x, i, z) + s] = cmake<C>(r, im);
-      }
-    }
-  }
-  __syncthreads();
-  // test x: Bb (nq,np,np) -> add into the x-pencil registers, then assemble
-#pragma unroll
-  for (int k = 0; k < NPEN; ++k) {
-    const int pid = lane + k * TPV;
-    if (pid >= NP * NP) break;
-    const int y = pid % NP, z = pid / NP;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C in[NQ];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) in[q] = Bb[2 * pidx<NQ>(q, y, z) + s];
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T r = 0, im = 0;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          r += tb.N[i][q] * in[q].x;
-          im += tb.N[i][q] * in[q].y;
-        }
-        yacc[k][s][i].x += r;
-        yacc[k][s][i].y += im;
-      }
-    }
-    if (vok) {
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        const long long I = gbc_node(d.mesh, cx, cy, cz, i, y, z);
-        if (I < 0) continue;
-        atomic_add_c<T>(&d.Y[(I * 2 + 0) * d.ldx + vec], yacc[k][0][i]);
-        atomic_add_c<T>(&d.Y[(I * 2 + 1) * d.ldx + vec], yacc[k][1][i]);
-      }
-    }
-  }
   }  // item loop
 }
 
 template <typename T, int NP, int NQ, int VB> constexpr size_t hx_local_smem() {
-  return sizeof(cplx<T>) * (size_t)VB * (3 * ((NQ + 1) * (NQ + 1) * NQ) * 2 + 1) +
-         sizeof(T) * 4 * NQ * NQ * NQ;
+  constexpr int BUF = pbuf_points<NQ>();
+  constexpr int VBASE = 3 * BUF * 2;
+  constexpr int VSTRIDE = VBASE + ((24 - VBASE % 16) % 16);
+  return sizeof(cplx<T>) * (size_t)VB * VSTRIDE;
 }
 
-// build the per-launch 1-D tables from the context's FP64 host tables
-template <typename T, int NP, int NQ>
-inline Tables1D<T, NP, NQ> make_tables(const gbc_ctx* c) {
-  Tables1D<T, NP, NQ> t;
-  const HostTables& h = c->tab;
-  for (int d = 0; d < 3; ++d) {
-    const double hd = c->h[d];
-    for (int i = 0; i < NP; ++i)
-      for (int j = 0; j < NP; ++j) {
-        t.B[d][i][j] = (T)(0.5 * hd * h.Bh[i * NP + j]);
-        t.Gr[d][i][j] = (T)(0.5 * (2.0 / hd) * h.Ah[i * NP + j]);
-        t.Gi[d][i][j] = (T)(-0.5 * c->k[d] * (h.Ch[i * NP + j] - h.Ch[j * NP + i]));
-      }
-  }
-  for (int i = 0; i < NP; ++i)
-    for (int q = 0; q < NQ; ++q) t.N[i][q] = (T)h.N1[i * NQ + q];
-  return t;
-}
-
-// One launch over n systems that share p, the cell edges and the k-point; the
-// first system's context provides the 1-D tables.
 template <typename T, int NP, int VB>
 cudaError_t launch_hx_group_p(const HxJob* jobs, int n, cudaStream_t s) {
   constexpr int NQ = NP + 1;   // nq = p + 2
@@ -454,7 +446,8 @@ cudaError_t launch_hx_group_p(const HxJob* jobs, int n, cudaStream_t s) {
   a.nitems = item;
   if (item <= 0) return cudaSuccess;
   const gbc_ctx* c0 = jobs[0].c;
-  const auto tb = make_tables<T, NP, NQ>(c0);
+  TablesEO<T, NP, NQ> tb;
+  if (!make_tables_eo<T, NP, NQ>(c0, &tb)) return cudaErrorInvalidValue;
   const bool kpt = (c0->k[0] != 0.0 || c0->k[1] != 0.0 || c0->k[2] != 0.0);
   constexpr size_t smem = hx_local_smem<T, NP, NQ, VB>();
   int dev = 0, nsm = 0, per_sm = 0;
