@@ -255,6 +255,18 @@ gbc_status gbc_get_tile(const gbc_ctx* ctx, int* vectors_per_cta);
 gbc_status gbc_apply_h_noalloc(gbc_ctx* ctx, const void* X, void* Y, int nvec, int ldx,
                                void* stream);
 
+/* ---- tensor-core building block ------------------------------------------------ */
+
+/* D = A B^T on the tcgen05 tensor cores in 3xTF32 (hi*hi + hi*lo + lo*hi of
+ * the TF32 split of each FP32 operand, FP32 accumulation in tensor memory).
+ * A: device [M][K], B: device [N][K], D: device [M][N], FP32 row-major;
+ * N in {16, 32, 48, 64, 128, 256} (GBC_EUNSUPPORTED otherwise), M, K >= 1.
+ * The projector contractions of the nonlocal step use the same tiles; this
+ * call exposes them for validation.  Synchronous; GBC_ETIMEOUT if a bounded
+ * wait on the tensor-core completion barrier expired. */
+gbc_status gbc_tc_gemm_nt(const float* A, const float* B, float* D, int M, int N, int K,
+                          void* stream);
+
 /* ---- tracing -------------------------------------------------------------- */
 
 /* Kernel families for gbc_get_timing. */

@@ -29,7 +29,8 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_cholgs", "gbc_rayleigh_ritz", "gbc_set_timing", "gbc_get_timing",
            "gbc_apply_h_noalloc", "gbc_batch_create", "gbc_batch_destroy",
            "gbc_batch_last_error", "gbc_batch_filter", "gbc_batch_launches", "gbc_tune",
-           "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta"]
+           "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta",
+           "gbc_tc_gemm_nt"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "gbc_filter_vjp": ([P, V, V, V, DP, DP, DP, I, I, I, D, D, D, I, V], I),
         "gbc_energy_grad": ([P, V, DP, V, DP, DP, DP, DP, I, I, V], I),
         "gbc_set_delta": ([P, DP], I),
+        "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
         "gbc_get_timing": ([P, I, DP, ct.POINTER(ct.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
@@ -384,3 +386,19 @@ class Batch:
         v = ct.c_int()
         self.lib.gbc_batch_launches(self.h, ct.byref(v))
         return v.value
+
+
+def tc_gemm_nt(A, B, stream=None):
+    """D = A @ B.T on the tcgen05 tensor cores (3xTF32); A [M, K], B [N, K] float32 CUDA."""
+    import torch
+    lib = load_library()
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    st = lib.gbc_tc_gemm_nt(ct.c_void_p(A.data_ptr()), ct.c_void_p(B.data_ptr()),
+                            ct.c_void_p(D.data_ptr()), M, N, K, _stream_ptr(stream))
+    if st != 0:
+        raise GbcError(st, "gbc_tc_gemm_nt failed")
+    return D
