@@ -166,13 +166,14 @@ def flops_per_cell_vector(p: int, nq: int, kpt: bool) -> int:
     return kin + interp + test + pointwise
 
 
-def build_contexts(g, prob, ks, prec):
+def build_contexts(g, prob, ks, prec, nl_engine=1):
     import torch
     ctxs = []
     for k in ks:
         c = g.Context(torch.cuda.current_device())
         c.set_problem(prob.with_(k=k))
         c.set_precision(prec)
+        c.set_nonlocal_engine(nl_engine)
         ctxs.append(c)
     return ctxs
 
@@ -200,7 +201,7 @@ def run_gpu(args):
     units_per_step = M * nvec * degree * len(ks)
 
     # ---- contexts, blocks, bounds (outside the timed region)
-    ctx32 = build_contexts(g, prob, ks, g.FP32)
+    ctx32 = build_contexts(g, prob, ks, g.FP32, args.nl_engine)
     X0 = syn.random_block(M, nvec, 0)
     v0 = torch.from_numpy(syn.random_start(M, 0)).cuda()
     bounds = []
@@ -235,6 +236,8 @@ def run_gpu(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     dist_barrier()
+    for c in ctx32:
+        c.sync_status()      # raises if a tensor-core wait expired inside the timed region
     ms_total = ev0.elapsed_time(ev1)
     ms_total = dist_max(ms_total, device="cuda" if world > 1 else "cpu")
     ms_step = ms_total / args.steps
@@ -275,7 +278,8 @@ def run_gpu(args):
            "config": {"workload": WORKLOAD, "config": args.config, "nodes": M, "nvec": nvec,
                       "degree": degree, "kpoints": len(ks), "precision": "FP32 filter (complex64)",
                       "l2": "inputs larger than L2 (3.6 GB per k-point block, 126 MB L2)",
-                      "parallelism": f"replicas x{world}"},
+                      "parallelism": f"replicas x{world}",
+                      "nonlocal_engine": ["simt", "tensor"][ctx32[0].nonlocal_engine()]},
            "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
            "kernels": kernels}
 
@@ -381,6 +385,7 @@ def run_batch(args):
         c = g.Context(torch.cuda.current_device())
         c.set_problem(prob)
         c.set_precision(g.FP32)
+        c.set_nonlocal_engine(args.nl_engine)
         c.tune(d["nvec"])
         M = prob.nnodes
         v0 = torch.from_numpy(syn.random_start(M, d["seed"])).cuda()
@@ -507,6 +512,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--cycles", type=int, default=3, help="ChFSI cycles of the accuracy leg")
+    ap.add_argument("--nl-engine", type=int, default=1, choices=[0, 1],
+                    help="FP32 projector contractions: 0 SIMT cores, 1 tcgen05 tensor cores")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

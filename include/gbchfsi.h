@@ -105,6 +105,27 @@ gbc_status gbc_set_projectors(gbc_ctx* ctx, int natoms, const int* npj, const in
 /* Arithmetic path for the block calls below.  Default GBC_FP64. */
 gbc_status gbc_set_precision(gbc_ctx* ctx, gbc_precision prec);
 
+/* Engine of the two projector contractions C = P^H X and Y += P C' of the
+ * nonlocal step (Eq. FEHnloc) in the FP32 precision:
+ *   GBC_NL_SIMT   = 0: FP32 FMA on the SIMT cores;
+ *   GBC_NL_TENSOR = 1: tcgen05 tensor cores in 3xTF32 with FP32 accumulation
+ *                      (default; used where the projector layout allows it:
+ *                      npj <= 64 and at most 16 atoms over any 128 owned
+ *                      support nodes, else the SIMT engine runs).
+ * FP64 always runs on the SIMT cores.  GBC_EINVAL for another value. */
+enum { GBC_NL_SIMT = 0, GBC_NL_TENSOR = 1 };
+gbc_status gbc_set_nonlocal_engine(gbc_ctx* ctx, int engine);
+/* Engine (GBC_NL_*) that the FP32 nonlocal step runs for the projectors set
+ * now: the requested one, or GBC_NL_SIMT where the layout excludes the tensor
+ * cores or no atoms are set. */
+gbc_status gbc_get_nonlocal_engine(const gbc_ctx* ctx, int* engine);
+
+/* Synchronise ``stream`` and report errors that kernels record on the device
+ * instead of trapping: GBC_ETIMEOUT if a bounded wait of a tensor-core kernel
+ * expired since the previous call (its results are then invalid), GBC_ECUDA
+ * for a CUDA error, else GBC_OK.  Clears the recorded flag. */
+gbc_status gbc_sync_status(gbc_ctx* ctx, void* stream);
+
 /* Number M of free FE nodes (spinor DOFs per vector = 2M). */
 gbc_status gbc_get_nnodes(const gbc_ctx* ctx, long long* nnodes);
 

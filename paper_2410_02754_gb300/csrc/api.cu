@@ -472,6 +472,34 @@ gbc_status gbc_set_precision(gbc_ctx* c, gbc_precision prec) {
   return GBC_OK;
 }
 
+gbc_status gbc_set_nonlocal_engine(gbc_ctx* c, int engine) {
+  if (!c) return GBC_EINVAL;
+  if (engine != GBC_NL_SIMT && engine != GBC_NL_TENSOR)
+    return gbc_fail(c, GBC_EINVAL, "unknown nonlocal engine");
+  c->nl_engine = engine;
+  return GBC_OK;
+}
+
+gbc_status gbc_get_nonlocal_engine(const gbc_ctx* c, int* engine) {
+  if (!c || !engine) return GBC_EINVAL;
+  *engine = (c->nl_engine == GBC_NL_TENSOR && tc_nonlocal_supported(c->proj)) ? GBC_NL_TENSOR
+                                                                               : GBC_NL_SIMT;
+  return GBC_OK;
+}
+
+gbc_status gbc_sync_status(gbc_ctx* c, void* stream) {
+  if (!c) return GBC_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int err = 0;
+  GBC_CU(c, tc_nonlocal_error(&err, s));
+  if (err) {
+    GBC_CU(c, tc_nonlocal_reset(s));
+    GBC_CU(c, cudaStreamSynchronize(s));
+    return gbc_fail(c, GBC_ETIMEOUT, "a tensor-core wait expired; results since the last check are invalid");
+  }
+  return GBC_OK;
+}
+
 gbc_status gbc_get_nnodes(const gbc_ctx* c, long long* nnodes) {
   if (!c || !nnodes) return GBC_EINVAL;
   if (!c->mesh_set) return GBC_ESTATE;

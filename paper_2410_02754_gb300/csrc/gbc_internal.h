@@ -12,6 +12,7 @@
 #define GBC_MAX_P 7
 #define GBC_MAX_NPJ 32
 #define GBC_MAX_BATCH 8     // systems per cell-apply launch
+#define GBC_TC_MAX_SLOTS 16 // atoms per tensor-core expansion chunk
 
 // ---------------------------------------------------------------------------
 // complex helpers (float2 / double2 carry (re, im))
@@ -106,6 +107,13 @@ struct ProjDev {
   int2* d_own_xinc = nullptr;        // other (atom, row) incidences
   int nexp_chunks = 0;
   int4* d_exp_chunks = nullptr;      // (owner atom, first owned index, count, 0)
+  // tensor-core expansion: chunks of <= 128 consecutive owned nodes, each with
+  // the list ("slots") of every atom whose support holds one of its nodes, so one
+  // GEMM over K = slots x 2npj gives the complete P C' of those rows
+  int ntc_exp = 0;
+  int4* d_tcexp_chunks = nullptr;    // (first owned index, count, slot offset, slot count)
+  int* d_tcexp_slots = nullptr;      // atom of each slot
+  int tc_max_slots = 0;              // largest slot count (> GBC_TC_MAX_SLOTS: no tensor path)
   // raw inputs kept on device for recomputation at a new k
   double* d_pvals = nullptr;
   int* d_entry_cell = nullptr;
@@ -145,6 +153,7 @@ struct gbc_ctx {
   size_t small_bytes = 0;
   int* d_flag = nullptr;
   int vb32 = 2;                      // FP32 cell-apply tile (vectors per CTA), set by the tuner
+  int nl_engine = 1;                 // FP32 projector contractions: 0 SIMT, 1 tensor cores
   // optional per-kernel-family timing (gbc_set_timing)
   bool timing = false;
   struct TimedLaunch { int family; cudaEvent_t a, b; };
@@ -208,6 +217,15 @@ cudaError_t launch_hx_local_f32(const gbc_ctx* c, const float2* X, float2* Y, in
 template <typename T>
 cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx,
                             cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s);
+// tcgen05 projector contractions (nonlocal_tc.cu), FP32 only
+bool tc_nonlocal_supported(const ProjDev& pj);
+cudaError_t launch_tc_project(const ProjDev& pj, const float2* X, int nvec, int ldx, float2* Cbuf,
+                              cudaStream_t s);
+cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, const float2* Cp,
+                             cudaStream_t s);
+cudaError_t tc_nonlocal_reset(cudaStream_t s);
+cudaError_t tc_nonlocal_error(int* err, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_nl_project(gbc_ctx* c, const cplx<T>* X, int nvec, int ldx, cplx<T>* Cbuf,
                               cudaStream_t s);

@@ -177,6 +177,8 @@ cudaError_t run_project(gbc_ctx* c, const cplx<T>* X, int nvec, int ldx, cplx<T>
   return cudaGetLastError();
 }
 
+bool use_tc(const gbc_ctx* c) { return c->nl_engine == GBC_NL_TENSOR && tc_nonlocal_supported(c->proj); }
+
 }  // namespace
 
 template <typename T>
@@ -184,12 +186,7 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
                             cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s) {
   const ProjDev& pj = c->proj;
   if (pj.natoms == 0 || nvec == 0 || pj.nchunks == 0 || pj.nexp_chunks == 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(Cbuf, 0, sizeof(cplx<T>) * (size_t)pj.rows_total * nvec, s);
-  if (e != cudaSuccess) return e;
-  if (pj.max_npj <= 4) e = run_project<T, 4>(c, X, nvec, ldx, Cbuf, s);
-  else if (pj.max_npj <= 8) e = run_project<T, 8>(c, X, nvec, ldx, Cbuf, s);
-  else if (pj.max_npj <= 18) e = run_project<T, 18>(c, X, nvec, ldx, Cbuf, s);
-  else e = run_project<T, GBC_MAX_NPJ>(c, X, nvec, ldx, Cbuf, s);
+  cudaError_t e = launch_nl_project<T>(c, X, nvec, ldx, Cbuf, s);
   if (e != cudaSuccess) return e;
   const cplx<T>* D = std::is_same<T, double>::value ? (const cplx<T>*)pj.d_delta64
                                                     : (const cplx<T>*)pj.d_delta32;
@@ -198,6 +195,9 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
                                    pj.d_atom_c_off, nvec);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_tc(c)) return launch_tc_expand(pj, Y, nvec, ldx, Cpbuf, s);
+  }
   const cplx<T>* P = std::is_same<T, double>::value ? (const cplx<T>*)pj.d_P64
                                                     : (const cplx<T>*)pj.d_P32;
   dim3 g3((unsigned)pj.nexp_chunks, (2 * nvec + kCols - 1) / kCols);
@@ -221,6 +221,9 @@ cudaError_t launch_nl_project(gbc_ctx* c, const cplx<T>* X, int nvec, int ldx, c
   if (pj.natoms == 0 || nvec == 0 || pj.nchunks == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(Cbuf, 0, sizeof(cplx<T>) * (size_t)pj.rows_total * nvec, s);
   if (e != cudaSuccess) return e;
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_tc(c)) return launch_tc_project(pj, X, nvec, ldx, Cbuf, s);
+  }
   if (pj.max_npj <= 4) return run_project<T, 4>(c, X, nvec, ldx, Cbuf, s);
   if (pj.max_npj <= 8) return run_project<T, 8>(c, X, nvec, ldx, Cbuf, s);
   if (pj.max_npj <= 18) return run_project<T, 18>(c, X, nvec, ldx, Cbuf, s);

@@ -1,0 +1,455 @@
+// Nonlocal spin-orbit step of H.X on the tcgen05 tensor cores (FP32 path).
+//
+// Paper: Eq. FEHnloc and step 3 of Sec. IV.B.2, C = P_a^H X, C' = Delta_a C,
+// Y += P_a C'.  The two large contractions are real GEMMs over real and
+// imaginary parts, computed in 3xTF32 (hi*hi + hi*lo + lo*hi, FP32-level
+// accuracy) with TMEM accumulators; the 2npj x 2npj coupling stays on the SIMT
+// cores.  A "real column" is one float of a node row [2][ldx] complex, i.e.
+// col = 2*(s*ldx + v) + part.
+//
+//  projection  (per atom, 32 support nodes per K tile)
+//              D[m][n] = sum_nodes X(node, col0 + m) Q_n(node), Q_2chi = Re P_chi,
+//              Q_2chi+1 = Im P_chi.  Neighbouring lanes hold the real and the
+//              imaginary column of one complex column, and C = sum conj(P) X is
+//              Re C = D[re][2chi] + D[im][2chi+1], Im C = D[im][2chi] - D[re][2chi+1].
+//  expansion   (per chunk of <= 128 owned nodes, K over the chunk's atom slots)
+//              D[m][n] = sum_k A[m][k] B[n][k] with A[m] = (Re P_b, Im P_b)(node m)
+//              for every slot atom b holding node m (zero otherwise), and
+//              B[re col] = (Re C'_b, -Im C'_b), B[im col] = (Im C'_b, Re C'_b):
+//              D is the real / imaginary part of sum_b P_b C'_b, added to Y once.
+#include <algorithm>
+#include <type_traits>
+
+#include "gbc_internal.h"
+#include "tc.cuh"
+
+namespace {
+
+__device__ int g_nltc_err;   // set when a bounded wait expired
+
+constexpr int kMT = 128;     // rows of D per CTA (one per thread)
+constexpr int kCT = 128;     // real columns per CTA
+constexpr int kMaxGridY = 65535;   // chunks per launch (grid y limit)
+
+struct TcCtx {
+  uint32_t tmem;
+  uint32_t mbar;
+};
+
+template <int NCOL>
+__device__ __forceinline__ TcCtx tc_begin(uint64_t* mbar, uint32_t* tslot) {
+  if ((threadIdx.x >> 5) == 0) {
+    tc::tmem_alloc(tc::smem_u32(tslot), NCOL);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(mbar), 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  return TcCtx{*tslot, tc::smem_u32(mbar)};
+}
+
+template <int NCOL>
+__device__ __forceinline__ void tc_end(const TcCtx& t) {
+  tc::fence_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(t.tmem, NCOL);
+}
+
+// make the staged tile visible to the tensor core and issue its 3 x 4 MMAs
+// (thread 0), completion signalled on the mbarrier
+// make the staged tile visible to the tensor core and issue its 3 x 4 MMAs
+// (thread 0), completion signalled on the mbarrier
+template <int N>
+__device__ __forceinline__ void tc_issue(const TcCtx& t, const float4* Ahi, const float4* Alo,
+                                         const float4* Bhi, const float4* Blo, bool first) {
+  tc::fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::fence_after_sync();
+    constexpr uint32_t idesc = tc::idesc_tf32(kMT, N);
+    const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo);
+    const uint32_t bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint32_t o = kk * 32;
+      const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+      tc::mma_tf32(t.tmem, tc::sdesc_sw128(ah + o), tc::sdesc_sw128(bh + o), idesc, acc);
+      tc::mma_tf32(t.tmem, tc::sdesc_sw128(ah + o), tc::sdesc_sw128(bl + o), idesc, 1u);
+      tc::mma_tf32(t.tmem, tc::sdesc_sw128(al + o), tc::sdesc_sw128(bh + o), idesc, 1u);
+    }
+    tc::mma_commit(t.mbar);
+  }
+}
+
+// all threads: wait (bounded) for the issued MMAs; the tile buffers are free after
+__device__ __forceinline__ bool tc_wait(const TcCtx& t, uint32_t& phase) {
+  const bool ok = tc::mbar_wait_bounded(t.mbar, phase);
+  phase ^= 1u;
+  tc::fence_after_sync();
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// after an expired wait: flag it and give the MMAs in flight a second bounded
+// wait before the TMEM is freed
+__device__ __forceinline__ void tc_fail(const TcCtx& t, uint32_t phase) {
+  if (threadIdx.x == 0) atomicExch(&g_nltc_err, 1);
+  tc::mbar_wait_bounded(t.mbar, phase ^ 1u);
+}
+
+__device__ __forceinline__ void put_split(float4* hi, float4* lo, int row, int chunk, float a,
+                                          float b, float c, float d) {
+  float h0, h1, h2, h3, l0, l1, l2, l3;
+  tc::split_tf32(a, h0, l0);
+  tc::split_tf32(b, h1, l1);
+  tc::split_tf32(c, h2, l2);
+  tc::split_tf32(d, h3, l3);
+  hi[tc::sw128(row, chunk)] = make_float4(h0, h1, h2, h3);
+  lo[tc::sw128(row, chunk)] = make_float4(l0, l1, l2, l3);
+}
+
+// ---- projection ------------------------------------------------------------------
+constexpr int kPrjChunk = 1024;   // support nodes per projection chunk (setup table)
+
+template <int NB>
+constexpr size_t project_smem() {
+  return 1024 + sizeof(float4) * 8 * (2 * kMT + 2 * NB) + sizeof(long long) * kPrjChunk + 64;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(128, 4)
+k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __restrict__ chunks,
+             const long long* __restrict__ nodes, const float2* __restrict__ P,
+             const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off,
+             const int* __restrict__ atom_c_off, float2* __restrict__ Cbuf, int chunk0) {
+  static_assert(NB % 16 == 0 && NB >= 16 && NB <= 128, "NB");
+  constexpr int NCOL = NB <= 32 ? 32 : NB <= 64 ? 64 : 128;
+  constexpr int NBC = NB / 16;   // B float4 chunks per thread (NB rows x 8 chunks / 128)
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
+  float4* Ahi = reinterpret_cast<float4*>(base);
+  float4* Alo = Ahi + kMT * 8;
+  float4* Bhi = Alo + kMT * 8;
+  float4* Blo = Bhi + NB * 8;
+  long long* Ns = reinterpret_cast<long long*>(Blo + NB * 8);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Ns + kPrjChunk);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int4 ch = chunks[chunk0 + blockIdx.y];   // (atom, first position, count, node offset)
+  const int atom = ch.x, j0 = ch.y, cnt = min(ch.z, kPrjChunk), noff = ch.w;
+  const int npj = atom_npj[atom];
+  const float2* Pa = P + atom_pv_off[atom] + (size_t)j0 * npj;
+  const int ncols = 4 * ldx;
+  const int tid = threadIdx.x;
+  const int col = blockIdx.x * kCT + tid;
+  const bool cok = col < ncols && ((col >> 1) % ldx) < nvec;
+  for (int t = tid; t < cnt; t += 128) Ns[t] = nodes[noff + j0 + t];
+  const TcCtx t = tc_begin<NCOL>(mbar, tslot);   // includes a __syncthreads
+
+  // kind::tf32 takes K-major operands only (an MN-major tf32 operand reads as
+  // zero on sm_103a), so A row m = column col0 + m is gathered column-wise: 32
+  // scalar loads per thread and tile, coalesced across the warp.  Two register
+  // buffers: the loads of tile i + 2 are issued while tile i is multiplied.
+  float xa0[32], xa1[32];
+  float xb0[NBC][4], xb1[NBC][4];
+  auto load = [&](float (&xa)[32], float (&xb)[NBC][4], int k0) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      xa[k] = (cok && k0 + k < cnt) ? __ldg(&Xr[Ns[k0 + k] * (long long)ncols + col]) : 0.f;
+#pragma unroll
+    for (int i = 0; i < NBC; ++i) {
+      const int q = tid + 128 * i, n = q >> 3, c = q & 7;
+      const int chi = n >> 1, im = n & 1;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k0 + 4 * c + j;
+        float val = 0.f;
+        if (chi < npj && k < cnt) {
+          const float2 p = __ldg(&Pa[(size_t)k * npj + chi]);
+          val = im ? p.y : p.x;
+        }
+        xb[i][j] = val;
+      }
+    }
+  };
+  auto stage = [&](const float (&xa)[32], const float (&xb)[NBC][4]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      put_split(Ahi, Alo, tid, c, xa[4 * c], xa[4 * c + 1], xa[4 * c + 2], xa[4 * c + 3]);
+#pragma unroll
+    for (int i = 0; i < NBC; ++i) {
+      const int q = tid + 128 * i;
+      put_split(Bhi, Blo, q >> 3, q & 7, xb[i][0], xb[i][1], xb[i][2], xb[i][3]);
+    }
+  };
+  uint32_t phase = 0;
+  bool ok = true;
+  if (cnt > 0) load(xa0, xb0, 0);
+  if (cnt > 32) load(xa1, xb1, 32);
+  for (int k0 = 0; k0 < cnt && ok; k0 += 64) {
+    stage(xa0, xb0);
+    tc_issue<NB>(t, Ahi, Alo, Bhi, Blo, k0 == 0);
+    if (k0 + 64 < cnt) load(xa0, xb0, k0 + 64);
+    ok = tc_wait(t, phase);
+    if (!ok || k0 + 32 >= cnt) break;
+    stage(xa1, xb1);
+    tc_issue<NB>(t, Ahi, Alo, Bhi, Blo, false);
+    if (k0 + 96 < cnt) load(xa1, xb1, k0 + 96);
+    ok = tc_wait(t, phase);
+  }
+  if (!ok) {
+    tc_fail(t, phase);
+  } else if (cnt > 0) {
+    const int warp = tid >> 5;
+    const int ci = col >> 1, s = ci / ldx, v = ci % ldx;
+    const bool store = (tid & 1) == 0 && cok;
+    const int r0 = atom_c_off[atom];
+#pragma unroll 1
+    for (int c0 = 0; c0 < NB; c0 += 16) {
+      float d[16];
+      tc::tmem_ld16(t.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, d);
+#pragma unroll
+      for (int j = 0; j < 16; j += 2) {
+        const float pr = __shfl_xor_sync(0xffffffffu, d[j], 1);       // D[im][2chi]
+        const float pi = __shfl_xor_sync(0xffffffffu, d[j + 1], 1);   // D[im][2chi+1]
+        const int chi = (c0 + j) >> 1;
+        if (store && chi < npj)
+          atomicAdd(&Cbuf[(size_t)(r0 + 2 * chi + s) * nvec + v],
+                    make_float2(d[j] + pi, pr - d[j + 1]));
+      }
+    }
+  }
+  tc_end<NCOL>(t);
+}
+
+// ---- expansion -------------------------------------------------------------------
+constexpr int kDsStride = 68;     // staged D half-tile row stride (floats), conflict-free
+
+constexpr size_t expand_smem() {
+  return 1024 + sizeof(float4) * 8 * 4 * 128                 // A, B hi / lo tiles
+         + sizeof(int) * 128 * GBC_TC_MAX_SLOTS              // row position per slot
+         + sizeof(int) * 4 * GBC_TC_MAX_SLOTS                // slot metadata
+         + sizeof(long long) * 128 + 64;                     // row nodes, barrier
+}
+
+__global__ void __launch_bounds__(128)
+k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __restrict__ chunks,
+            const int* __restrict__ slots, const long long* __restrict__ own_node,
+            const int* __restrict__ own_pos, const int* __restrict__ own_xptr,
+            const int2* __restrict__ own_xinc, const float2* __restrict__ P,
+            const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off,
+            const int* __restrict__ atom_c_off, const float2* __restrict__ Cp, int chunk0) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
+  float4* Ahi = reinterpret_cast<float4*>(base);
+  float4* Alo = Ahi + 128 * 8;
+  float4* Bhi = Alo + 128 * 8;
+  float4* Blo = Bhi + 128 * 8;
+  float* Ds = reinterpret_cast<float*>(base);     // epilogue staging over the free tiles
+  int* rowpos = reinterpret_cast<int*>(Blo + 128 * 8);   // [slot][row]
+  int* s_npj = rowpos + 128 * GBC_TC_MAX_SLOTS;
+  int* s_pv = s_npj + GBC_TC_MAX_SLOTS;
+  int* s_c = s_pv + GBC_TC_MAX_SLOTS;
+  int* s_atom = s_c + GBC_TC_MAX_SLOTS;
+  long long* s_node = reinterpret_cast<long long*>(s_atom + GBC_TC_MAX_SLOTS);   // [128]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_node + 128);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int4 ch = chunks[chunk0 + blockIdx.y];   // (first owned index, count, slot offset, slots)
+  const int u0 = ch.x, cnt = min(ch.y, 128), nsl = min(ch.w, GBC_TC_MAX_SLOTS);
+  const int tid = threadIdx.x;
+  const int ncols = 4 * ldx;
+  const int col0 = blockIdx.x * kCT;
+  if (tid < nsl) {
+    const int b = slots[ch.z + tid];
+    s_atom[tid] = b;
+    s_npj[tid] = atom_npj[b];
+    s_pv[tid] = atom_pv_off[b];
+    s_c[tid] = atom_c_off[b];
+  }
+  for (int i = tid; i < 128 * GBC_TC_MAX_SLOTS; i += 128) rowpos[i] = -1;
+  const TcCtx t = tc_begin<128>(mbar, tslot);   // includes a __syncthreads
+  if (tid < cnt) {   // slot 0 is the owner of every row of the chunk
+    const int u = u0 + tid;
+    s_node[tid] = own_node[u];
+    rowpos[tid] = own_pos[u];
+    for (int k = own_xptr[u]; k < own_xptr[u + 1]; ++k) {
+      const int2 inc = own_xinc[k];
+      for (int sl = 1; sl < nsl; ++sl)
+        if (s_atom[sl] == inc.x) rowpos[sl * 128 + tid] = inc.y;
+    }
+  }
+  __syncthreads();
+
+  // B row n = real column col0 + n
+  const int col = col0 + tid;
+  const int ci = col >> 1, cs = ci / ldx, cv = ci % ldx;
+  const bool cok = col < ncols && cv < nvec;
+  const bool cim = (col & 1) != 0;
+  const int ktot = nsl * ks;
+  float xa[32], xb[32];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {   // pairs (2chi, 2chi + 1) of one slot
+      const int kg = k0 + 2 * j;
+      const int sl = kg / ks, chi = (kg - sl * ks) >> 1;
+      float2 p = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+      if (kg < ktot && chi < s_npj[sl]) {
+        const int pos = rowpos[sl * 128 + tid];
+        if (pos >= 0) p = __ldg(&P[s_pv[sl] + (size_t)pos * s_npj[sl] + chi]);
+        if (cok) c = __ldg(&Cp[(size_t)(s_c[sl] + 2 * chi + cs) * nvec + cv]);
+      }
+      xa[2 * j] = p.x;
+      xa[2 * j + 1] = p.y;
+      xb[2 * j] = cim ? c.y : c.x;
+      xb[2 * j + 1] = cim ? c.x : -c.y;
+    }
+  };
+  uint32_t phase = 0;
+  bool ok = true;
+  load(0);
+  for (int k0 = 0; k0 < ktot && ok; k0 += 32) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      put_split(Ahi, Alo, tid, c, xa[4 * c], xa[4 * c + 1], xa[4 * c + 2], xa[4 * c + 3]);
+      put_split(Bhi, Blo, tid, c, xb[4 * c], xb[4 * c + 1], xb[4 * c + 2], xb[4 * c + 3]);
+    }
+    tc_issue<128>(t, Ahi, Alo, Bhi, Blo, k0 == 0);
+    if (k0 + 32 < ktot) load(k0 + 32);
+    ok = tc_wait(t, phase);
+  }
+  if (!ok) {
+    tc_fail(t, phase);
+  } else if (ktot > 0) {
+    // epilogue in two 64-column halves: TMEM -> shared (row per thread) ->
+    // coalesced read-modify-write of 256 contiguous bytes of each node row
+    const int warp = tid >> 5, lane = tid & 31;
+    const bool full = ldx == nvec;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        float d[16];
+        tc::tmem_ld16(t.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(64 * h + c0), d);
+        float4* dst = reinterpret_cast<float4*>(Ds + tid * kDsStride + c0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          dst[j] = make_float4(d[4 * j], d[4 * j + 1], d[4 * j + 2], d[4 * j + 3]);
+      }
+      __syncthreads();
+      const int cc = 64 * h + 4 * (lane & 15);   // this lane's 4 columns of the half
+      const int gc = col0 + cc;
+      const int rbase = warp * 2 + (lane >> 4);    // rows rbase + 8 i
+      if (full && gc + 4 <= ncols) {
+        // all 16 row loads in flight before the first add
+        float4 yv[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int r = rbase + 8 * i;
+          if (r < cnt) yv[i] = *reinterpret_cast<const float4*>(Yr + s_node[r] * (long long)ncols + gc);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int r = rbase + 8 * i;
+          if (r < cnt) {
+            const float4 dv = *reinterpret_cast<const float4*>(Ds + r * kDsStride + 4 * (lane & 15));
+            yv[i].x += dv.x;
+            yv[i].y += dv.y;
+            yv[i].z += dv.z;
+            yv[i].w += dv.w;
+            *reinterpret_cast<float4*>(Yr + s_node[r] * (long long)ncols + gc) = yv[i];
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int r = rbase; r < cnt; r += 8) {
+          const float* dv = Ds + r * kDsStride + 4 * (lane & 15);
+          float* y = Yr + s_node[r] * (long long)ncols + gc;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int c = gc + j;
+            if (c < ncols && ((c >> 1) % ldx) < nvec) y[j] += dv[j];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  tc_end<128>(t);
+}
+
+template <int NB>
+cudaError_t run_tc_project(const ProjDev& pj, const float2* X, int nvec, int ldx, float2* Cbuf,
+                           cudaStream_t s) {
+  auto k = k_tc_project<NB>;
+  constexpr size_t smem = project_smem<NB>();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned ntile = (unsigned)((4 * ldx + kCT - 1) / kCT);
+  for (int c0 = 0; c0 < pj.nchunks; c0 += kMaxGridY) {
+    dim3 grid(ntile, (unsigned)std::min(kMaxGridY, pj.nchunks - c0));
+    k<<<grid, 128, smem, s>>>(reinterpret_cast<const float*>(X), ldx, nvec, pj.d_chunks,
+                              pj.d_nodes, pj.d_P32, pj.d_atom_npj, pj.d_atom_pv_off,
+                              pj.d_atom_c_off, Cbuf, c0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+bool tc_nonlocal_supported(const ProjDev& pj) {
+  return pj.natoms > 0 && pj.max_npj <= 64 && pj.ntc_exp > 0 &&
+         pj.tc_max_slots <= GBC_TC_MAX_SLOTS;
+}
+
+cudaError_t launch_tc_project(const ProjDev& pj, const float2* X, int nvec, int ldx, float2* Cbuf,
+                              cudaStream_t s) {
+  const int nb = 16 * ((2 * pj.max_npj + 15) / 16);
+  switch (nb) {
+    case 16: return run_tc_project<16>(pj, X, nvec, ldx, Cbuf, s);
+    case 32: return run_tc_project<32>(pj, X, nvec, ldx, Cbuf, s);
+    case 48: return run_tc_project<48>(pj, X, nvec, ldx, Cbuf, s);
+    case 64: return run_tc_project<64>(pj, X, nvec, ldx, Cbuf, s);
+    case 80: return run_tc_project<80>(pj, X, nvec, ldx, Cbuf, s);
+    case 96: return run_tc_project<96>(pj, X, nvec, ldx, Cbuf, s);
+    case 112: return run_tc_project<112>(pj, X, nvec, ldx, Cbuf, s);
+    case 128: return run_tc_project<128>(pj, X, nvec, ldx, Cbuf, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, const float2* Cp,
+                             cudaStream_t s) {
+  constexpr size_t smem = expand_smem();
+  cudaError_t e =
+      cudaFuncSetAttribute(k_tc_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned ntile = (unsigned)((4 * ldx + kCT - 1) / kCT);
+  for (int c0 = 0; c0 < pj.ntc_exp; c0 += kMaxGridY) {
+    dim3 grid(ntile, (unsigned)std::min(kMaxGridY, pj.ntc_exp - c0));
+    k_tc_expand<<<grid, 128, smem, s>>>(reinterpret_cast<float*>(Y), ldx, nvec, 2 * pj.max_npj,
+                                        pj.d_tcexp_chunks, pj.d_tcexp_slots, pj.d_own_node,
+                                        pj.d_own_pos, pj.d_own_xptr, pj.d_own_xinc, pj.d_P32,
+                                        pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off, Cp, c0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// reset / read the bounded-wait flag of the tensor-core nonlocal kernels
+cudaError_t tc_nonlocal_reset(cudaStream_t s) {
+  static const int zero = 0;
+  return cudaMemcpyToSymbolAsync(g_nltc_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+}
+cudaError_t tc_nonlocal_error(int* err, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyFromSymbolAsync(err, g_nltc_err, sizeof(int), 0,
+                                            cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}

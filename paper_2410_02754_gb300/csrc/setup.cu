@@ -485,6 +485,45 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
     }
   }
   oxptr.push_back((int)oxinc.size());
+  std::vector<int4> tcchunks;
+  std::vector<int> tcslots;
+  {
+    // consecutive owned nodes of one owner, at most 128 rows and GBC_TC_MAX_SLOTS
+    // distinct atoms per chunk
+    std::vector<int> cur;
+    int u0 = 0, cnt = 0;
+    auto flush = [&]() {
+      if (cnt == 0) return;   // slot 0 stays the chunk's owner atom
+      tcchunks.push_back(make_int4(u0, cnt, (int)tcslots.size(), (int)cur.size()));
+      tcslots.insert(tcslots.end(), cur.begin(), cur.end());
+      cur.clear();
+      cnt = 0;
+    };
+    int u = 0;
+    for (int a = 0; a < natoms; ++a) {
+      for (size_t j = 0; j < own_node[a].size(); ++j, ++u) {
+        std::vector<int> add;
+        if (std::find(cur.begin(), cur.end(), a) == cur.end()) add.push_back(a);
+        for (int k = oxptr[u]; k < oxptr[u + 1]; ++k) {
+          const int b = oxinc[k].x;
+          if (std::find(cur.begin(), cur.end(), b) == cur.end() &&
+              std::find(add.begin(), add.end(), b) == add.end())
+            add.push_back(b);
+        }
+        if (cnt == 128 || cur.size() + add.size() > GBC_TC_MAX_SLOTS) {
+          flush();
+          add.clear();
+          add.push_back(a);
+          for (int k = oxptr[u]; k < oxptr[u + 1]; ++k)
+            if (std::find(add.begin(), add.end(), oxinc[k].x) == add.end()) add.push_back(oxinc[k].x);
+        }
+        if (cnt == 0) u0 = u;
+        cur.insert(cur.end(), add.begin(), add.end());
+        ++cnt;
+      }
+      flush();
+    }
+  }
   if (oxinc.empty()) oxinc.push_back(make_int2(0, 0));   // keep a valid allocation
   pj.nuniq = (long long)onode.size();
   pj.nexp_chunks = (int)echunks.size();
@@ -507,6 +546,11 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
   GBC_TRY(upload(c, (void**)&pj.d_own_xptr, oxptr.data(), sizeof(int) * oxptr.size()));
   GBC_TRY(upload(c, (void**)&pj.d_own_xinc, oxinc.data(), sizeof(int2) * oxinc.size()));
   GBC_TRY(upload(c, (void**)&pj.d_exp_chunks, echunks.data(), sizeof(int4) * echunks.size()));
+  pj.ntc_exp = (int)tcchunks.size();
+  pj.tc_max_slots = 0;
+  for (const int4& q : tcchunks) pj.tc_max_slots = std::max(pj.tc_max_slots, q.w);
+  GBC_TRY(upload(c, (void**)&pj.d_tcexp_chunks, tcchunks.data(), sizeof(int4) * tcchunks.size()));
+  GBC_TRY(upload(c, (void**)&pj.d_tcexp_slots, tcslots.data(), sizeof(int) * tcslots.size()));
   GBC_TRY(upload(c, (void**)&pj.d_pvals, pvals, sizeof(double) * pvals_total));
   GBC_TRY(upload(c, (void**)&pj.d_entry_cell, entry_cell.data(), sizeof(int) * entry_cell.size()));
   GBC_TRY(upload(c, (void**)&pj.d_entry_img, entry_img.data(), sizeof(int) * entry_img.size()));
@@ -526,7 +570,7 @@ void free_projectors(ProjDev& pj) {
   void* ptrs[] = {pj.d_nodes, pj.d_atom_npj, pj.d_atom_node_off, pj.d_atom_pv_off,
                   pj.d_atom_delta_off, pj.d_atom_c_off, pj.d_P64, pj.d_P32, pj.d_delta64,
                   pj.d_delta32, pj.d_chunks, pj.d_own_node, pj.d_own_pos, pj.d_own_xptr,
-                  pj.d_own_xinc, pj.d_exp_chunks,
+                  pj.d_own_xinc, pj.d_exp_chunks, pj.d_tcexp_chunks, pj.d_tcexp_slots,
                   pj.d_pvals, pj.d_entry_cell, pj.d_entry_img, pj.d_entry_atom, pj.d_entry_pos};
   for (void* p : ptrs) cudaFree(p);
   pj = ProjDev();

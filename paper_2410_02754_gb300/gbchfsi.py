@@ -30,7 +30,8 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_apply_h_noalloc", "gbc_batch_create", "gbc_batch_destroy",
            "gbc_batch_last_error", "gbc_batch_filter", "gbc_batch_launches", "gbc_tune",
            "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta",
-           "gbc_tc_gemm_nt"]
+           "gbc_tc_gemm_nt", "gbc_set_nonlocal_engine", "gbc_get_nonlocal_engine",
+           "gbc_sync_status"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -84,6 +85,9 @@ def load_library(path: str = LIB_PATH):
         "gbc_energy_grad": ([P, V, DP, V, DP, DP, DP, DP, I, I, V], I),
         "gbc_set_delta": ([P, DP], I),
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
+        "gbc_set_nonlocal_engine": ([P, I], I),
+        "gbc_get_nonlocal_engine": ([P, IP], I),
+        "gbc_sync_status": ([P, V], I),
         "gbc_get_timing": ([P, I, DP, ct.POINTER(ct.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
@@ -189,6 +193,20 @@ class Context:
     def set_precision(self, prec):
         self._chk(self.lib.gbc_set_precision(self.h, int(prec)))
         self.prec = prec
+
+    def set_nonlocal_engine(self, engine):
+        """0 = SIMT cores, 1 = tcgen05 tensor cores (FP32 projector contractions)."""
+        self._chk(self.lib.gbc_set_nonlocal_engine(self.h, int(engine)))
+
+    def nonlocal_engine(self):
+        """Engine the FP32 nonlocal step runs for the current projectors."""
+        e = ct.c_int()
+        self._chk(self.lib.gbc_get_nonlocal_engine(self.h, ct.byref(e)))
+        return e.value
+
+    def sync_status(self, stream=None):
+        """Synchronise and raise if a device-side bounded wait expired."""
+        self._chk(self.lib.gbc_sync_status(self.h, _stream_ptr(stream)))
 
     def mass(self):
         md = np.empty(self.nnodes, np.float64)
@@ -402,3 +420,4 @@ def tc_gemm_nt(A, B, stream=None):
     if st != 0:
         raise GbcError(st, "gbc_tc_gemm_nt failed")
     return D
+
