@@ -60,12 +60,17 @@ __device__ __forceinline__ void tc_end(const TcCtx& t) {
 }
 
 // make the staged tile visible to the tensor core and issue its 3 x 4 MMAs
-// (thread 0), completion signalled on the mbarrier
-// make the staged tile visible to the tensor core and issue its 3 x 4 MMAs
-// (thread 0), completion signalled on the mbarrier
-template <int N>
-__device__ __forceinline__ void tc_issue(const TcCtx& t, const float4* Ahi, const float4* Alo,
-                                         const float4* Bhi, const float4* Blo, bool first) {
+// (thread 0), completion signalled on the mbarrier.  The tensor core's FP32
+// accumulator truncates toward zero at every accumulating MMA, a bias that
+// grows with the chain length, so the main products hi*hi go to their own
+// accumulator D0 (4 accumulations per tile) and the small cross terms
+// hi*lo + lo*hi (relative size 2^-11, their truncation is negligible) to D1 =
+// D0 + d1col; callers keep D0 chains short and add D0 + D1 in FP32.  Without
+// SPLIT all three products accumulate into D0.
+template <int N, bool SPLIT = true>
+__device__ __forceinline__ void tc_issue(const TcCtx& t, uint32_t d1col, const float4* Ahi,
+                                         const float4* Alo, const float4* Bhi, const float4* Blo,
+                                         bool first) {
   tc::fence_proxy_async();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -73,13 +78,14 @@ __device__ __forceinline__ void tc_issue(const TcCtx& t, const float4* Ahi, cons
     constexpr uint32_t idesc = tc::idesc_tf32(kMT, N);
     const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo);
     const uint32_t bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+    const uint32_t d0 = t.tmem, d1 = SPLIT ? t.tmem + d1col : t.tmem;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
       const uint32_t o = kk * 32;
       const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
-      tc::mma_tf32(t.tmem, tc::sdesc_sw128(ah + o), tc::sdesc_sw128(bh + o), idesc, acc);
-      tc::mma_tf32(t.tmem, tc::sdesc_sw128(ah + o), tc::sdesc_sw128(bl + o), idesc, 1u);
-      tc::mma_tf32(t.tmem, tc::sdesc_sw128(al + o), tc::sdesc_sw128(bh + o), idesc, 1u);
+      tc::mma_tf32(d0, tc::sdesc_sw128(ah + o), tc::sdesc_sw128(bh + o), idesc, acc);
+      tc::mma_tf32(d1, tc::sdesc_sw128(ah + o), tc::sdesc_sw128(bl + o), idesc, SPLIT ? acc : 1u);
+      tc::mma_tf32(d1, tc::sdesc_sw128(al + o), tc::sdesc_sw128(bh + o), idesc, 1u);
     }
     tc::mma_commit(t.mbar);
   }
@@ -113,6 +119,7 @@ __device__ __forceinline__ void put_split(float4* hi, float4* lo, int row, int c
 
 // ---- projection ------------------------------------------------------------------
 constexpr int kPrjChunk = 1024;   // support nodes per projection chunk (setup table)
+constexpr int kSeg = 8;           // K tiles per accumulation segment (256 nodes)
 
 template <int NB>
 constexpr size_t project_smem() {
@@ -126,7 +133,7 @@ k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __rest
              const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off,
              const int* __restrict__ atom_c_off, float2* __restrict__ Cbuf, int chunk0) {
   static_assert(NB % 16 == 0 && NB >= 16 && NB <= 128, "NB");
-  constexpr int NCOL = NB <= 32 ? 32 : NB <= 64 ? 64 : 128;
+  constexpr int NCOL = NB <= 32 ? 32 : NB <= 64 ? 64 : 128;   // per accumulator (D0, D1)
   constexpr int NBC = NB / 16;   // B float4 chunks per thread (NB rows x 8 chunks / 128)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
@@ -147,7 +154,7 @@ k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __rest
   const int col = blockIdx.x * kCT + tid;
   const bool cok = col < ncols && ((col >> 1) % ldx) < nvec;
   for (int t = tid; t < cnt; t += 128) Ns[t] = nodes[noff + j0 + t];
-  const TcCtx t = tc_begin<NCOL>(mbar, tslot);   // includes a __syncthreads
+  const TcCtx t = tc_begin<2 * NCOL>(mbar, tslot);   // includes a __syncthreads
 
   // kind::tf32 takes K-major operands only (an MN-major tf32 operand reads as
   // zero on sm_103a), so A row m = column col0 + m is gathered column-wise: 32
@@ -185,44 +192,54 @@ k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __rest
       put_split(Bhi, Blo, q >> 3, q & 7, xb[i][0], xb[i][1], xb[i][2], xb[i][3]);
     }
   };
+  // C += D0 + D1 for this CTA's columns (round-to-nearest FP32 atomics); lane
+  // pairs hold the real / imaginary column of one complex column
+  const int warp = tid >> 5;
+  const int ci = col >> 1, s = ci / ldx, v = ci % ldx;
+  const bool store = (tid & 1) == 0 && cok;
+  const int r0 = atom_c_off[atom];
+  auto flush = [&]() {
+#pragma unroll 1
+    for (int c0 = 0; c0 < NB; c0 += 8) {
+      uint32_t a0[8], a1[8];
+      const uint32_t ta = t.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      tc::tmem_ld8_nowait(ta, a0);
+      tc::tmem_ld8_nowait(ta + NCOL, a1);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        const float dr = __uint_as_float(a0[j]) + __uint_as_float(a1[j]);
+        const float di = __uint_as_float(a0[j + 1]) + __uint_as_float(a1[j + 1]);
+        const float pr = __shfl_xor_sync(0xffffffffu, dr, 1);   // D[im][2chi]
+        const float pi = __shfl_xor_sync(0xffffffffu, di, 1);   // D[im][2chi+1]
+        const int chi = (c0 + j) >> 1;
+        if (store && chi < npj)
+          atomicAdd(&Cbuf[(size_t)(r0 + 2 * chi + s) * nvec + v], make_float2(dr + pi, pr - di));
+      }
+    }
+    tc::fence_before_sync();   // the next tile's MMAs overwrite D0 / D1
+  };
   uint32_t phase = 0;
   bool ok = true;
   if (cnt > 0) load(xa0, xb0, 0);
   if (cnt > 32) load(xa1, xb1, 32);
   for (int k0 = 0; k0 < cnt && ok; k0 += 64) {
     stage(xa0, xb0);
-    tc_issue<NB>(t, Ahi, Alo, Bhi, Blo, k0 == 0);
+    tc_issue<NB>(t, NCOL, Ahi, Alo, Bhi, Blo, k0 % (32 * kSeg) == 0);
     if (k0 + 64 < cnt) load(xa0, xb0, k0 + 64);
     ok = tc_wait(t, phase);
     if (!ok || k0 + 32 >= cnt) break;
     stage(xa1, xb1);
-    tc_issue<NB>(t, Ahi, Alo, Bhi, Blo, false);
+    tc_issue<NB>(t, NCOL, Ahi, Alo, Bhi, Blo, false);
     if (k0 + 96 < cnt) load(xa1, xb1, k0 + 96);
     ok = tc_wait(t, phase);
+    if (ok && (k0 + 64) % (32 * kSeg) == 0 && k0 + 64 < cnt) flush();
   }
-  if (!ok) {
+  if (!ok)
     tc_fail(t, phase);
-  } else if (cnt > 0) {
-    const int warp = tid >> 5;
-    const int ci = col >> 1, s = ci / ldx, v = ci % ldx;
-    const bool store = (tid & 1) == 0 && cok;
-    const int r0 = atom_c_off[atom];
-#pragma unroll 1
-    for (int c0 = 0; c0 < NB; c0 += 16) {
-      float d[16];
-      tc::tmem_ld16(t.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, d);
-#pragma unroll
-      for (int j = 0; j < 16; j += 2) {
-        const float pr = __shfl_xor_sync(0xffffffffu, d[j], 1);       // D[im][2chi]
-        const float pi = __shfl_xor_sync(0xffffffffu, d[j + 1], 1);   // D[im][2chi+1]
-        const int chi = (c0 + j) >> 1;
-        if (store && chi < npj)
-          atomicAdd(&Cbuf[(size_t)(r0 + 2 * chi + s) * nvec + v],
-                    make_float2(d[j] + pi, pr - d[j + 1]));
-      }
-    }
-  }
-  tc_end<NCOL>(t);
+  else if (cnt > 0)
+    flush();
+  tc_end<2 * NCOL>(t);
 }
 
 // ---- expansion -------------------------------------------------------------------
@@ -271,6 +288,8 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
     s_c[tid] = atom_c_off[b];
   }
   for (int i = tid; i < 128 * GBC_TC_MAX_SLOTS; i += 128) rowpos[i] = -1;
+  // one accumulator: the chain is short (K = slots x 2 npj, about 4 tiles), and
+  // 128 TMEM columns keep 3 CTAs per SM
   const TcCtx t = tc_begin<128>(mbar, tslot);   // includes a __syncthreads
   if (tid < cnt) {   // slot 0 is the owner of every row of the chunk
     const int u = u0 + tid;
@@ -317,7 +336,7 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
       put_split(Ahi, Alo, tid, c, xa[4 * c], xa[4 * c + 1], xa[4 * c + 2], xa[4 * c + 3]);
       put_split(Bhi, Blo, tid, c, xb[4 * c], xb[4 * c + 1], xb[4 * c + 2], xb[4 * c + 3]);
     }
-    tc_issue<128>(t, Ahi, Alo, Bhi, Blo, k0 == 0);
+    tc_issue<128, false>(t, 0, Ahi, Alo, Bhi, Blo, k0 == 0);
     if (k0 + 32 < ktot) load(k0 + 32);
     ok = tc_wait(t, phase);
   }
