@@ -219,8 +219,8 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
                             cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s);
 // tcgen05 projector contractions (nonlocal_tc.cu), FP32 only
 bool tc_nonlocal_supported(const ProjDev& pj);
-cudaError_t launch_tc_project(const ProjDev& pj, const float2* X, int nvec, int ldx, float2* Cbuf,
-                              cudaStream_t s);
+cudaError_t launch_tc_project(const ProjDev& pj, long long M, const float2* X, int nvec, int ldx,
+                              float2* Cbuf, cudaStream_t s);
 cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, const float2* Cp,
                              cudaStream_t s);
 cudaError_t tc_nonlocal_reset(cudaStream_t s);

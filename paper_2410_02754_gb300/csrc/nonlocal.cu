@@ -222,7 +222,7 @@ cudaError_t launch_nl_project(gbc_ctx* c, const cplx<T>* X, int nvec, int ldx, c
   cudaError_t e = cudaMemsetAsync(Cbuf, 0, sizeof(cplx<T>) * (size_t)pj.rows_total * nvec, s);
   if (e != cudaSuccess) return e;
   if constexpr (std::is_same<T, float>::value) {
-    if (use_tc(c)) return launch_tc_project(pj, X, nvec, ldx, Cbuf, s);
+    if (use_tc(c)) return launch_tc_project(pj, c->mesh.M, X, nvec, ldx, Cbuf, s);
   }
   if (pj.max_npj <= 4) return run_project<T, 4>(c, X, nvec, ldx, Cbuf, s);
   if (pj.max_npj <= 8) return run_project<T, 8>(c, X, nvec, ldx, Cbuf, s);

@@ -20,6 +20,10 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <mutex>
+
 #include "gbc_internal.h"
 #include "tc.cuh"
 
@@ -145,6 +149,7 @@ k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __rest
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Ns + kPrjChunk);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
+  if (*reinterpret_cast<volatile int*>(&g_nltc_err)) return;   // an earlier CTA gave up
   const int4 ch = chunks[chunk0 + blockIdx.y];   // (atom, first position, count, node offset)
   const int atom = ch.x, j0 = ch.y, cnt = min(ch.z, kPrjChunk), noff = ch.w;
   const int npj = atom_npj[atom];
@@ -242,6 +247,265 @@ k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __rest
   tc_end<2 * NCOL>(t);
 }
 
+// ---- projection, TMA-fed pipeline -------------------------------------------------
+// The same product with the X rows brought in by TMA instead of register loads:
+// warp 0 issues, per tile of 32 support nodes, eight tile::gather4 copies (4 rows
+// x 128 columns each) and one bulk copy of the tile's P rows into a ring of
+// kStages raw stages (completion: mbarrier transaction bytes); warps 2-5 turn a
+// raw stage into the split K-major A / B tiles (two buffers) and flush the
+// accumulators; warp 1 issues the MMAs.  No CTA-wide barrier sits between a
+// load and its use, so up to kStages tiles (64 KB) per SM are in flight.
+// Requires ldx == nvec, 4 ldx >= 128, 16-byte aligned X and even P offsets.
+constexpr int kStages = 6;
+constexpr int kConv = 256;                  // converter threads (warps 2-9)
+constexpr int kPrjThreads = 64 + kConv;     // + producer and MMA warps
+
+__device__ __forceinline__ bool wait_uniform(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+  bool ok = false;
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    if (tc::mbar_try_wait(mbar, parity)) {
+      ok = true;
+      break;
+    }
+    if ((i & 255u) == 255u && *abort_flag) break;
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  if (!ok && (threadIdx.x & 31) == 0) {
+    *abort_flag = 1;
+    atomicExch(&g_nltc_err, 1);
+  }
+  return ok;
+}
+
+template <int NB>
+constexpr size_t project_tma_smem() {
+  return 1024 + 4 * (size_t)NB * 128           // B hi / lo, two buffers
+         + (size_t)kStages * 16384             // raw X stages
+         + (size_t)kStages * NB * 128          // raw P stages
+         + 4 * kPrjChunk                       // node rows of the chunk
+         + 8 * (2 * kStages + 4) + 32;         // barriers, TMEM slot, flags
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kPrjThreads, 1)
+k_tc_project_tma(const __grid_constant__ CUtensorMap xmap, int ldx, int nvec,
+                 const int4* __restrict__ chunks, const long long* __restrict__ nodes,
+                 const float2* __restrict__ P, const int* __restrict__ atom_npj,
+                 const int* __restrict__ atom_pv_off, const int* __restrict__ atom_c_off,
+                 float2* __restrict__ Cbuf, int chunk0) {
+  static_assert(NB % 16 == 0 && NB >= 16 && NB <= 64, "NB");
+  constexpr int NCOL = NB <= 32 ? 32 : 64;   // per accumulator
+  // six accumulators: (hi*hi, hi*lo, lo*hi) x tile parity, so that the MMA
+  // chains of one tile (4 deep each) and of consecutive tiles run side by side
+  constexpr int NACC = 6;
+  // A (the X tile, split) lives in tensor memory after the accumulators: buffer b
+  // holds hi in columns ACOL + 64 b .. + 31 and lo in the next 32
+  constexpr int ACOL = NCOL * NACC;
+  constexpr int TCOLS = 512;
+  static_assert(ACOL + 128 <= TCOLS, "TMEM");
+  constexpr uint32_t kBT = NB * 128;         // bytes of one B tile (hi or lo)
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* bb = base;
+  float* rawX = reinterpret_cast<float*>(bb + 4 * kBT);                     // [S][32][128]
+  float2* rawP = reinterpret_cast<float2*>(bb + 4 * kBT + kStages * 16384);  // [S][NB * 16]
+  int* rows = reinterpret_cast<int*>(bb + 4 * kBT + kStages * 16384 + kStages * kBT);   // [1024]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rows + kPrjChunk);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  volatile int* prog = reinterpret_cast<volatile int*>(tslot + 2);   // issued / waited / MMA'd tiles
+  auto Bh = [&](int b) { return reinterpret_cast<float4*>(bb + b * kBT); };
+  auto Bl = [&](int b) { return reinterpret_cast<float4*>(bb + (2 + b) * kBT); };
+  auto full = [&](int s) { return tc::smem_u32(bars + s); };
+  auto empty = [&](int s) { return tc::smem_u32(bars + kStages + s); };
+  auto afull = [&](int b) { return tc::smem_u32(bars + 2 * kStages + b); };
+  auto aempty = [&](int b) { return tc::smem_u32(bars + 2 * kStages + 2 + b); };
+
+  if (*reinterpret_cast<volatile int*>(&g_nltc_err)) return;   // an earlier CTA gave up
+  const int4 ch = chunks[chunk0 + blockIdx.y];   // (atom, first position, count, node offset)
+  const int atom = ch.x, j0 = ch.y, cnt = min(ch.z, kPrjChunk), noff = ch.w;
+  const int npj = atom_npj[atom];
+  const float2* Pa = P + atom_pv_off[atom] + (size_t)j0 * npj;
+  const int col0 = blockIdx.x * kCT;
+  const int ncols = 4 * ldx;
+  const int T = (cnt + 31) / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (int i = threadIdx.x; i < 32 * T; i += blockDim.x)
+    rows[i] = i < cnt ? (int)nodes[noff + j0 + i] : -1;   // -1: rows read as zero
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(tslot), TCOLS);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < kStages; ++i) {
+      tc::mbar_init(full(i), 1);
+      tc::mbar_init(empty(i), kConv);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(afull(b), kConv);
+      tc::mbar_init(aempty(b), 1);
+    }
+    *abort_flag = 0;
+    prog[0] = prog[1] = prog[2] = 0;
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ---- producer
+    for (int t = 0; t < T; ++t) {
+      const int s = t % kStages;
+      if (t >= kStages && !wait_uniform(empty(s), ((t / kStages) - 1) & 1, abort_flag)) break;
+      const int nval = min(32, cnt - t * 32);
+      const uint32_t pbytes = ((uint32_t)(nval * npj * 8) + 15u) & ~15u;
+      if (lane == 0) tc::mbar_arrive_expect_tx(full(s), 16384u + pbytes);
+      __syncwarp();
+      if (lane < 8) {
+        const int* r = rows + t * 32 + 4 * lane;
+        tc::tma_gather4(tc::smem_u32(rawX + s * 4096 + lane * 512), &xmap, col0, r[0], r[1], r[2],
+                        r[3], full(s));
+      }
+      if (lane == 0) {
+        tc::bulk_g2s(tc::smem_u32(rawP + s * (kBT / 8)), Pa + (size_t)t * 32 * npj, pbytes, full(s));
+        prog[0] = t + 1;
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issue
+    constexpr uint32_t idesc = tc::idesc_tf32(kMT, NB);
+    for (int t = 0; t < T; ++t) {
+      const int b = t & 1;
+      if (!wait_uniform(afull(b), (t >> 1) & 1, abort_flag)) break;
+      tc::fence_after_sync();
+      if (lane == 0) {
+        const uint32_t ah = tmem + (uint32_t)(ACOL + 64 * b), al = ah + 32;
+        const uint32_t bh = tc::smem_u32(Bh(b)), bl = tc::smem_u32(Bl(b));
+        const bool first = t % kSeg < 2;            // first tile of this parity in the segment
+        const uint32_t d = tmem + (uint32_t)(3 * NCOL * b);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t o = kk * 32;
+          const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+          tc::mma_tf32_ts(d, ah + 8 * kk, tc::sdesc_sw128(bh + o), idesc, acc);
+          tc::mma_tf32_ts(d + NCOL, ah + 8 * kk, tc::sdesc_sw128(bl + o), idesc, acc);
+          tc::mma_tf32_ts(d + 2 * NCOL, al + 8 * kk, tc::sdesc_sw128(bh + o), idesc, acc);
+        }
+        tc::mma_commit(aempty(b));
+        prog[2] = t + 1;
+      }
+      __syncwarp();
+    }
+  } else {
+    // ---- converters (warps 2-9): warp w owns TMEM lanes / A rows 32 (w % 4) ..
+    // + 31 and, with h = (w - 2) / 4, the K half 16 h .. 16 h + 15 of every tile
+    // and every other 8-column group of the flush; B is converted by all of them
+    const int m = 32 * (warp & 3) + lane;
+    const int h = (warp - 2) >> 2;
+    const int ct = threadIdx.x - 64;           // converter thread 0 .. kConv - 1
+    const int col = col0 + m;
+    const bool cok = col < ncols && ((col >> 1) % ldx) < nvec;
+    const int ci = col >> 1, sp = ci / ldx, v = ci % ldx;
+    const bool store = (lane & 1) == 0 && cok;
+    const int r0c = atom_c_off[atom];
+    // nacc: 3 when the segment so far has only its first (even) tile, else 6
+    auto flush = [&](int nacc) {
+#pragma unroll 1
+      for (int c0 = 8 * h; c0 < NB; c0 += 16) {
+        float sum[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sum[j] = 0.f;
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+        uint32_t a[NACC][8];
+        // hi*hi of both parities first, then the small cross terms
+#pragma unroll
+        for (int q = 0; q < NACC; ++q) {
+          const int acc_i = nacc == NACC ? (q % 2) * 3 + q / 2 : q;   // 0, 3, 1, 4, 2, 5
+          if (q < nacc) tc::tmem_ld8_nowait(ta + (uint32_t)(acc_i * NCOL), a[q]);
+        }
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < NACC; ++q)
+          if (q < nacc)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sum[j] += __uint_as_float(a[q][j]);
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          const float dr = sum[j];
+          const float di = sum[j + 1];
+          const float pr = __shfl_xor_sync(0xffffffffu, dr, 1);   // D[im][2chi]
+          const float pi = __shfl_xor_sync(0xffffffffu, di, 1);   // D[im][2chi+1]
+          const int chi = (c0 + j) >> 1;
+          if (store && chi < npj)
+            atomicAdd(&Cbuf[(size_t)(r0c + 2 * chi + sp) * nvec + v], make_float2(dr + pi, pr - di));
+        }
+      }
+      tc::fence_before_sync();
+    };
+    for (int t = 0; t < T; ++t) {
+      const int s = t % kStages, b = t & 1;
+      if (!wait_uniform(full(s), (t / kStages) & 1, abort_flag)) break;
+      if (ct == 0) prog[1] = t + 1;
+      if (t >= 2 && !wait_uniform(aempty(b), ((t - 2) >> 1) & 1, abort_flag)) break;
+      tc::fence_after_sync();   // the MMAs that read A buffer b have completed
+      {
+        // this thread's A row (TMEM lane m), K half h: split and store to TMEM
+        const float* rx = rawX + s * 4096 + 16 * h * 128;
+        float hi[16], lo[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) tc::split_tf32(cok ? rx[k * 128 + m] : 0.f, hi[k], lo[k]);
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ACOL + 64 * b + 16 * h);
+        tc::tmem_st16(ta, hi);
+        tc::tmem_st16(ta + 32, lo);
+      }
+      // B: chunk (row n, K chunk c), n fastest across the lanes (conflict-free)
+      const float2* rp = rawP + s * (kBT / 8);
+      const int nval = min(32, cnt - t * 32);
+#pragma unroll 1
+      for (int qq = ct; qq < NB * 8; qq += kConv) {
+        const int n = qq % NB, c = qq / NB;
+        const int chi = n >> 1, im = n & 1;
+        float y[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = 4 * c + j;
+          float val = 0.f;
+          if (chi < npj && k < nval) {
+            const float2 pv = rp[k * npj + chi];
+            val = im ? pv.y : pv.x;
+          }
+          y[j] = val;
+        }
+        put_split(Bh(b), Bl(b), n, c, y[0], y[1], y[2], y[3]);
+      }
+      tc::tmem_wait_st();
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      tc::mbar_arrive(empty(s));
+      tc::mbar_arrive(afull(b));
+      if (t % kSeg == kSeg - 1 || t == T - 1) {
+        if (!wait_uniform(aempty(b), (t >> 1) & 1, abort_flag)) break;
+        tc::fence_after_sync();
+        flush(t % kSeg == 0 ? 3 : NACC);
+      }
+    }
+  }
+  // ---- teardown: after an expired wait, give the copies and MMAs in flight a
+  // bounded wait of their own before the TMEM is freed
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) {
+    for (int t = prog[1]; t < prog[0]; ++t) tc::mbar_wait_bounded(full(t % kStages), (t / kStages) & 1);
+    if (prog[2] > 0) tc::mbar_wait_bounded(aempty((prog[2] - 1) & 1), ((prog[2] - 1) >> 1) & 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+}
+
 // ---- expansion -------------------------------------------------------------------
 constexpr int kDsStride = 68;     // staged D half-tile row stride (floats), conflict-free
 
@@ -275,6 +539,7 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
   uint64_t* mbar = reinterpret_cast<uint64_t*>(s_node + 128);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
+  if (*reinterpret_cast<volatile int*>(&g_nltc_err)) return;   // an earlier CTA gave up
   const int4 ch = chunks[chunk0 + blockIdx.y];   // (first owned index, count, slot offset, slots)
   const int u0 = ch.x, cnt = min(ch.y, 128), nsl = min(ch.w, GBC_TC_MAX_SLOTS);
   const int tid = threadIdx.x;
@@ -419,6 +684,52 @@ cudaError_t run_tc_project(const ProjDev& pj, const float2* X, int nvec, int ldx
   return cudaSuccess;
 }
 
+using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// X viewed as a 2-D tensor [M rows][4 ldx floats]; box = 128 floats x 1 row
+bool make_x_map(CUtensorMap* map, const float2* X, long long M, int ldx) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)(4 * (long long)ldx), (cuuint64_t)M};
+  const cuuint64_t strides[1] = {(cuuint64_t)(4 * (long long)ldx) * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kCT, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(X), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NB>
+cudaError_t run_tc_project_tma(const ProjDev& pj, const CUtensorMap& map, int nvec, int ldx,
+                               float2* Cbuf, cudaStream_t s) {
+  auto k = k_tc_project_tma<NB>;
+  constexpr size_t smem = project_tma_smem<NB>();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned ntile = (unsigned)((4 * ldx + kCT - 1) / kCT);
+  for (int c0 = 0; c0 < pj.nchunks; c0 += kMaxGridY) {
+    dim3 grid(ntile, (unsigned)std::min(kMaxGridY, pj.nchunks - c0));
+    k<<<grid, kPrjThreads, smem, s>>>(map, ldx, nvec, pj.d_chunks, pj.d_nodes, pj.d_P32, pj.d_atom_npj,
+                              pj.d_atom_pv_off, pj.d_atom_c_off, Cbuf, c0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 bool tc_nonlocal_supported(const ProjDev& pj) {
@@ -426,9 +737,23 @@ bool tc_nonlocal_supported(const ProjDev& pj) {
          pj.tc_max_slots <= GBC_TC_MAX_SLOTS;
 }
 
-cudaError_t launch_tc_project(const ProjDev& pj, const float2* X, int nvec, int ldx, float2* Cbuf,
-                              cudaStream_t s) {
+cudaError_t launch_tc_project(const ProjDev& pj, long long M, const float2* X, int nvec, int ldx,
+                              float2* Cbuf, cudaStream_t s) {
   const int nb = 16 * ((2 * pj.max_npj + 15) / 16);
+  // TMA-fed pipeline where the block layout allows it
+  if (ldx == nvec && 4 * ldx >= kCT && nb <= 64 && M < (1LL << 31) &&
+      (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    CUtensorMap map;
+    if (make_x_map(&map, X, M, ldx)) {
+      switch (nb) {
+        case 16: return run_tc_project_tma<16>(pj, map, nvec, ldx, Cbuf, s);
+        case 32: return run_tc_project_tma<32>(pj, map, nvec, ldx, Cbuf, s);
+        case 48: return run_tc_project_tma<48>(pj, map, nvec, ldx, Cbuf, s);
+        case 64: return run_tc_project_tma<64>(pj, map, nvec, ldx, Cbuf, s);
+        default: break;
+      }
+    }
+  }
   switch (nb) {
     case 16: return run_tc_project<16>(pj, X, nvec, ldx, Cbuf, s);
     case 32: return run_tc_project<32>(pj, X, nvec, ldx, Cbuf, s);

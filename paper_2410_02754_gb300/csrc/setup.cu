@@ -335,7 +335,7 @@ gbc_status setup_projectors(gbc_ctx* c) {
   t.np1 = np1;
   t.nq = nq;
   const long long ntab = (long long)pj.pv_off.back();
-  GBC_CU(c, cudaMemset(pj.d_P64, 0, sizeof(double2) * ntab));
+  GBC_CU(c, cudaMemset(pj.d_P64, 0, sizeof(double2) * (ntab + 2)));
   // per-entry base offset into pvals
   std::vector<long long> base(pj.nentries);
   {
@@ -358,7 +358,7 @@ gbc_status setup_projectors(gbc_ctx* c) {
                                    pj.d_entry_atom, pj.d_entry_pos, dbase, pj.d_atom_npj,
                                    pj.d_atom_pv_off, pj.d_P64);
   GBC_CU(c, cudaGetLastError());
-  k_to_f32<<<(unsigned)((ntab + 255) / 256), 256>>>(pj.d_P64, pj.d_P32, ntab);
+  k_to_f32<<<(unsigned)((ntab + 2 + 255) / 256), 256>>>(pj.d_P64, pj.d_P32, ntab + 2);
   GBC_CU(c, cudaGetLastError());
   GBC_CU(c, cudaDeviceSynchronize());
   cudaFree(dbase);
@@ -439,7 +439,8 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
     }
     for (size_t j = 0; j < nodes.size(); ++j) inc.push_back({nodes[j], make_int2(a, (int)j)});
     all_nodes.insert(all_nodes.end(), nodes.begin(), nodes.end());
-    pj.pv_off[a + 1] = pj.pv_off[a] + (int)nodes.size() * npj[a];
+    // per-atom tables start on 16-byte boundaries (bulk copies of P rows)
+    pj.pv_off[a + 1] = pj.pv_off[a] + (((int)nodes.size() * npj[a] + 1) & ~1);
     pj.delta_off[a + 1] = pj.delta_off[a] + 4 * npj[a] * npj[a];
     pj.c_off[a + 1] = pj.c_off[a] + 2 * npj[a];
   }
@@ -561,8 +562,9 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
   pj.d_P64 = nullptr;
   pj.d_P32 = nullptr;
   const long long ntab = pj.pv_off[natoms];
-  GBC_CU(c, cudaMalloc(&pj.d_P64, sizeof(double2) * std::max<long long>(ntab, 1)));
-  GBC_CU(c, cudaMalloc(&pj.d_P32, sizeof(float2) * std::max<long long>(ntab, 1)));
+  // + 2 entries: a bulk copy of the last rows may round up by one float2
+  GBC_CU(c, cudaMalloc(&pj.d_P64, sizeof(double2) * (ntab + 2)));
+  GBC_CU(c, cudaMalloc(&pj.d_P32, sizeof(float2) * (ntab + 2)));
   return GBC_OK;
 }
 

@@ -6,6 +6,8 @@ expansion's atom slots (chunks of 128 owned nodes split when more than 16 atoms
 touch them), K tiles that straddle slot boundaries (npj = 18 gives 36 reals a
 slot), a single projector (N = 16), ragged and padded column tiles, and the
 fallback to the SIMT engine when one node lies in more than 16 supports.
+Blocks with ldx == nvec and at least 32 vectors take the TMA-fed projection
+(tile::gather4 of X rows), the others the register-fed one.
 """
 import numpy as np
 import pytest
@@ -56,6 +58,7 @@ def max_node_multiplicity(prob):
 CASES = [
     # ncell, p, periodic, natoms, rc, channels, nvec, ldx
     ((4, 4, 4), 3, (1, 1, 1), 6, 2.0, "spd", 37, 40),       # 2 projection chunks per atom
+    ((4, 4, 4), 3, (1, 1, 1), 6, 2.0, "spd", 48, 48),       # TMA-fed projection, ragged tiles
     ((6, 6, 6), 2, (1, 1, 1), 40, 0.8, "spd", 64, 64),      # many slot splits, mult 13
     ((3, 2, 3), 4, (1, 0, 1), 3, 1.2, "s", 5, 8),           # npj = 1, Dirichlet faces
     ((5, 5, 5), 2, (1, 1, 1), 40, 1.2, "spd", 9, 9),        # mult 30 > 16: SIMT fallback
@@ -119,3 +122,39 @@ def test_tensor_nonlocal_filter_and_engine_errors(g):
                 ctx.set_nonlocal_engine(2)
         ctx.close()
     assert rel(res[1], res[0]) < 1e-5
+
+
+def test_tensor_nonlocal_long_chains_unbiased(g):
+    """Config-1 atoms (19k-node supports: projection chains of 1024 nodes, 4-14
+    expansion slots) with Delta scaled by 1e5 so that the nonlocal part dominates
+    H X: (H X - H_loc X) from the FP32 tensor engine against the FP64 oracle's
+    nonlocal apply.  The tensor core's accumulator truncates toward zero, which
+    unmitigated scaled C = P^H X by about -5e-6 here; the check bounds both the
+    relative error and its systematic part (the error's component along the
+    exact result)."""
+    import dataclasses
+    prob = syn.config("c1", kindex=1)
+    # at Delta x 1 the nonlocal part is ~2.5e-4 of the local one on random blocks
+    prob = prob.with_(atoms=[dataclasses.replace(a, delta=a.delta * 1e5) for a in prob.atoms])
+    d = fe.Discretisation(prob)
+    X = syn.random_block(d.mesh.nnodes, 32, 21)   # 32 vectors: TMA-fed projection
+    ref = d.apply_nonlocal(X)
+    out = {}
+    for name, p in (("full", prob), ("local", prob.with_(atoms=[]))):
+        ctx = g.Context(0)
+        ctx.set_problem(p)
+        ctx.set_precision(1)
+        if name == "full":
+            assert ctx.nonlocal_engine() == 1
+        Xd = torch.from_numpy(X).to(torch.complex64).cuda()
+        Yd = torch.empty_like(Xd)
+        ctx.apply_h(Xd, Yd)
+        ctx.sync_status()
+        out[name] = Yd.cpu().numpy().astype(np.complex128)
+        ctx.close()
+    nl = out["full"] - out["local"]
+    err = nl - ref
+    assert np.linalg.norm(out["local"]) < 0.1 * np.linalg.norm(ref)
+    assert rel(nl, ref) < 3e-6, rel(nl, ref)
+    scale = np.real(np.vdot(ref, err)) / np.real(np.vdot(ref, ref))
+    assert abs(scale) < 1e-6, scale
