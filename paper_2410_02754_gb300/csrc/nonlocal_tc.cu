@@ -248,17 +248,35 @@ k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __rest
 }
 
 // ---- projection, TMA-fed pipeline -------------------------------------------------
-// The same product with the X rows brought in by TMA instead of register loads:
-// warp 0 issues, per tile of 32 support nodes, eight tile::gather4 copies (4 rows
-// x 128 columns each) and one bulk copy of the tile's P rows into a ring of
-// kStages raw stages (completion: mbarrier transaction bytes); warps 2-5 turn a
-// raw stage into the split K-major A / B tiles (two buffers) and flush the
-// accumulators; warp 1 issues the MMAs.  No CTA-wide barrier sits between a
-// load and its use, so up to kStages tiles (64 KB) per SM are in flight.
-// Requires ldx == nvec, 4 ldx >= 128, 16-byte aligned X and even P offsets.
+// The same product with the X rows brought in by TMA and A kept in tensor
+// memory.  Warp roles:
+//   warp 0        producer: per tile of 32 support nodes, eight tile::gather4
+//                 copies (4 rows x 128 columns each) and one bulk copy of the
+//                 tile's P rows into a ring of kStages raw stages (completion:
+//                 mbarrier transaction bytes);
+//   warp 1        MMA issue (A from tensor memory, B from shared memory);
+//   warps 2..17   converters: warp w owns TMEM lanes 32 (w % 4) .. + 31 (A rows =
+//                 real columns) and the K quarter 8 q .. 8 q + 7, q = (w - 2) / 4;
+//                 they split a raw stage into TF32 hi / lo, store A into tensor
+//                 memory (tcgen05.st) and the K-major B tile into shared memory,
+//                 kAB buffers each, so that kAB tiles of MMAs can be in flight;
+//   warps 18..21  epilogue: flush each finished 256-node segment's accumulators
+//                 through round-to-nearest FP32 atomics while the next segment
+//                 is multiplied into the other accumulator set.
+// Accumulators: two sets (segment parity, 128 TMEM columns apart): one N = 2 NB
+// MMA per K step multiplies A_hi by the stacked [B_lo; B_hi] tile (hi*lo in
+// columns 0..NB-1, hi*hi in NB..2NB-1) and one N = NB MMA adds lo*hi to the
+// cross-term columns: 8 MMAs per tile instead of 12 (the tensor core's time per
+// MMA at these shapes is mostly fixed), and the truncating hi*hi chain stays 4
+// MMAs per tile, 32 per segment.  No CTA-wide
+// barrier sits between a load and its use.  Requires ldx == nvec, 4 ldx >= 128,
+// 16-byte aligned X and even P offsets.
 constexpr int kStages = 6;
-constexpr int kConv = 256;                  // converter threads (warps 2-9)
-constexpr int kPrjThreads = 64 + kConv;     // + producer and MMA warps
+constexpr int kAB = 4;                           // A / B buffers
+constexpr int kConvWarps = 16;
+constexpr int kConv = 32 * kConvWarps;           // converter threads
+constexpr int kEpiWarp0 = 2 + kConvWarps;        // first epilogue warp
+constexpr int kPrjThreads = 32 * (kEpiWarp0 + 4);
 
 __device__ __forceinline__ bool wait_uniform(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
   bool ok = false;
@@ -279,11 +297,11 @@ __device__ __forceinline__ bool wait_uniform(uint32_t mbar, uint32_t parity, vol
 
 template <int NB>
 constexpr size_t project_tma_smem() {
-  return 1024 + 4 * (size_t)NB * 128           // B hi / lo, two buffers
+  return 1024 + 2 * kAB * (size_t)NB * 128     // B hi / lo, kAB buffers
          + (size_t)kStages * 16384             // raw X stages
          + (size_t)kStages * NB * 128          // raw P stages
          + 4 * kPrjChunk                       // node rows of the chunk
-         + 8 * (2 * kStages + 4) + 32;         // barriers, TMEM slot, flags
+         + 8 * (2 * kStages + 2 * kAB + 4) + 32;   // barriers, TMEM slot, flags
 }
 
 template <int NB>
@@ -294,33 +312,29 @@ k_tc_project_tma(const __grid_constant__ CUtensorMap xmap, int ldx, int nvec,
                  const int* __restrict__ atom_pv_off, const int* __restrict__ atom_c_off,
                  float2* __restrict__ Cbuf, int chunk0) {
   static_assert(NB % 16 == 0 && NB >= 16 && NB <= 64, "NB");
-  constexpr int NCOL = NB <= 32 ? 32 : 64;   // per accumulator
-  // six accumulators: (hi*hi, hi*lo, lo*hi) x tile parity, so that the MMA
-  // chains of one tile (4 deep each) and of consecutive tiles run side by side
-  constexpr int NACC = 6;
-  // A (the X tile, split) lives in tensor memory after the accumulators: buffer b
-  // holds hi in columns ACOL + 64 b .. + 31 and lo in the next 32
-  constexpr int ACOL = NCOL * NACC;
+  constexpr int ACOL = 256;                    // A buffers (hi 32 + lo 32 columns) after the two sets
   constexpr int TCOLS = 512;
-  static_assert(ACOL + 128 <= TCOLS, "TMEM");
-  constexpr uint32_t kBT = NB * 128;         // bytes of one B tile (hi or lo)
+  static_assert(ACOL + 64 * kAB <= TCOLS, "TMEM");
+  constexpr uint32_t kBT = NB * 128;           // bytes of one B tile (hi or lo)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  unsigned char* bb = base;
-  float* rawX = reinterpret_cast<float*>(bb + 4 * kBT);                     // [S][32][128]
-  float2* rawP = reinterpret_cast<float2*>(bb + 4 * kBT + kStages * 16384);  // [S][NB * 16]
-  int* rows = reinterpret_cast<int*>(bb + 4 * kBT + kStages * 16384 + kStages * kBT);   // [1024]
+  constexpr uint32_t kBB = 2 * kAB * kBT;     // all B buffers
+  float* rawX = reinterpret_cast<float*>(base + kBB);                         // [S][32][128]
+  float2* rawP = reinterpret_cast<float2*>(base + kBB + kStages * 16384);      // [S][NB * 16]
+  int* rows = reinterpret_cast<int*>(base + kBB + kStages * 16384 + kStages * kBT);
   uint64_t* bars = reinterpret_cast<uint64_t*>(rows + kPrjChunk);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 2 * kAB + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   volatile int* prog = reinterpret_cast<volatile int*>(tslot + 2);   // issued / waited / MMA'd tiles
-  auto Bh = [&](int b) { return reinterpret_cast<float4*>(bb + b * kBT); };
-  auto Bl = [&](int b) { return reinterpret_cast<float4*>(bb + (2 + b) * kBT); };
+  auto Bl = [&](int b) { return reinterpret_cast<float4*>(base + 2 * b * kBT); };
+  auto Bh = [&](int b) { return reinterpret_cast<float4*>(base + (2 * b + 1) * kBT); };
   auto full = [&](int s) { return tc::smem_u32(bars + s); };
   auto empty = [&](int s) { return tc::smem_u32(bars + kStages + s); };
   auto afull = [&](int b) { return tc::smem_u32(bars + 2 * kStages + b); };
-  auto aempty = [&](int b) { return tc::smem_u32(bars + 2 * kStages + 2 + b); };
+  auto aempty = [&](int b) { return tc::smem_u32(bars + 2 * kStages + kAB + b); };
+  auto segdone = [&](int p) { return tc::smem_u32(bars + 2 * kStages + 2 * kAB + p); };
+  auto setfree = [&](int p) { return tc::smem_u32(bars + 2 * kStages + 2 * kAB + 2 + p); };
 
   if (*reinterpret_cast<volatile int*>(&g_nltc_err)) return;   // an earlier CTA gave up
   const int4 ch = chunks[chunk0 + blockIdx.y];   // (atom, first position, count, node offset)
@@ -330,6 +344,7 @@ k_tc_project_tma(const __grid_constant__ CUtensorMap xmap, int ldx, int nvec,
   const int col0 = blockIdx.x * kCT;
   const int ncols = 4 * ldx;
   const int T = (cnt + 31) / 32;
+  const int nseg = (T + kSeg - 1) / kSeg;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   for (int i = threadIdx.x; i < 32 * T; i += blockDim.x)
@@ -343,9 +358,13 @@ k_tc_project_tma(const __grid_constant__ CUtensorMap xmap, int ldx, int nvec,
       tc::mbar_init(full(i), 1);
       tc::mbar_init(empty(i), kConv);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kAB; ++b) {
       tc::mbar_init(afull(b), kConv);
       tc::mbar_init(aempty(b), 1);
+    }
+    for (int p = 0; p < 2; ++p) {
+      tc::mbar_init(segdone(p), 1);
+      tc::mbar_init(setfree(p), 128);
     }
     *abort_flag = 0;
     prog[0] = prog[1] = prog[2] = 0;
@@ -377,95 +396,57 @@ k_tc_project_tma(const __grid_constant__ CUtensorMap xmap, int ldx, int nvec,
     }
   } else if (warp == 1) {
     // ---- MMA issue
-    constexpr uint32_t idesc = tc::idesc_tf32(kMT, NB);
+    constexpr uint32_t idesc2 = tc::idesc_tf32(kMT, 2 * NB);   // A_hi x [B_lo; B_hi]
+    constexpr uint32_t idesc = tc::idesc_tf32(kMT, NB);        // A_lo x B_hi
     for (int t = 0; t < T; ++t) {
-      const int b = t & 1;
-      if (!wait_uniform(afull(b), (t >> 1) & 1, abort_flag)) break;
+      const int b = t % kAB, sg = t / kSeg, p = sg & 1;
+      const bool first = t % kSeg == 0;
+      if (first && sg >= 2 && !wait_uniform(setfree(p), ((sg >> 1) - 1) & 1, abort_flag)) break;
+      if (!wait_uniform(afull(b), (t / kAB) & 1, abort_flag)) break;
       tc::fence_after_sync();
       if (lane == 0) {
         const uint32_t ah = tmem + (uint32_t)(ACOL + 64 * b), al = ah + 32;
         const uint32_t bh = tc::smem_u32(Bh(b)), bl = tc::smem_u32(Bl(b));
-        const bool first = t % kSeg < 2;            // first tile of this parity in the segment
-        const uint32_t d = tmem + (uint32_t)(3 * NCOL * b);
+        const uint32_t d = tmem + (uint32_t)(128 * p);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const uint32_t o = kk * 32;
           const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
-          tc::mma_tf32_ts(d, ah + 8 * kk, tc::sdesc_sw128(bh + o), idesc, acc);
-          tc::mma_tf32_ts(d + NCOL, ah + 8 * kk, tc::sdesc_sw128(bl + o), idesc, acc);
-          tc::mma_tf32_ts(d + 2 * NCOL, al + 8 * kk, tc::sdesc_sw128(bh + o), idesc, acc);
+          // B_hi follows B_lo: the N = 2 NB descriptor at B_lo covers both
+          tc::mma_tf32_ts(d, ah + 8 * kk, tc::sdesc_sw128(bl + o), idesc2, acc);
+          tc::mma_tf32_ts(d, al + 8 * kk, tc::sdesc_sw128(bh + o), idesc, 1u);
         }
         tc::mma_commit(aempty(b));
+        if (t % kSeg == kSeg - 1 || t == T - 1) tc::mma_commit(segdone(p));
         prog[2] = t + 1;
       }
       __syncwarp();
     }
-  } else {
-    // ---- converters (warps 2-9): warp w owns TMEM lanes / A rows 32 (w % 4) ..
-    // + 31 and, with h = (w - 2) / 4, the K half 16 h .. 16 h + 15 of every tile
-    // and every other 8-column group of the flush; B is converted by all of them
-    const int m = 32 * (warp & 3) + lane;
-    const int h = (warp - 2) >> 2;
+  } else if (warp < kEpiWarp0) {
+    // ---- converters
+    const int m = 32 * (warp & 3) + lane;      // A row = TMEM lane = real column col0 + m
+    const int q = (warp - 2) >> 2;             // K quarter
     const int ct = threadIdx.x - 64;           // converter thread 0 .. kConv - 1
     const int col = col0 + m;
     const bool cok = col < ncols && ((col >> 1) % ldx) < nvec;
-    const int ci = col >> 1, sp = ci / ldx, v = ci % ldx;
-    const bool store = (lane & 1) == 0 && cok;
-    const int r0c = atom_c_off[atom];
-    // nacc: 3 when the segment so far has only its first (even) tile, else 6
-    auto flush = [&](int nacc) {
-#pragma unroll 1
-      for (int c0 = 8 * h; c0 < NB; c0 += 16) {
-        float sum[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) sum[j] = 0.f;
-        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
-        uint32_t a[NACC][8];
-        // hi*hi of both parities first, then the small cross terms
-#pragma unroll
-        for (int q = 0; q < NACC; ++q) {
-          const int acc_i = nacc == NACC ? (q % 2) * 3 + q / 2 : q;   // 0, 3, 1, 4, 2, 5
-          if (q < nacc) tc::tmem_ld8_nowait(ta + (uint32_t)(acc_i * NCOL), a[q]);
-        }
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int q = 0; q < NACC; ++q)
-          if (q < nacc)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) sum[j] += __uint_as_float(a[q][j]);
-#pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-          const float dr = sum[j];
-          const float di = sum[j + 1];
-          const float pr = __shfl_xor_sync(0xffffffffu, dr, 1);   // D[im][2chi]
-          const float pi = __shfl_xor_sync(0xffffffffu, di, 1);   // D[im][2chi+1]
-          const int chi = (c0 + j) >> 1;
-          if (store && chi < npj)
-            atomicAdd(&Cbuf[(size_t)(r0c + 2 * chi + sp) * nvec + v], make_float2(dr + pi, pr - di));
-        }
-      }
-      tc::fence_before_sync();
-    };
     for (int t = 0; t < T; ++t) {
-      const int s = t % kStages, b = t & 1;
+      const int s = t % kStages, b = t % kAB;
       if (!wait_uniform(full(s), (t / kStages) & 1, abort_flag)) break;
       if (ct == 0) prog[1] = t + 1;
-      if (t >= 2 && !wait_uniform(aempty(b), ((t - 2) >> 1) & 1, abort_flag)) break;
-      tc::fence_after_sync();   // the MMAs that read A buffer b have completed
+      if (t >= kAB && !wait_uniform(aempty(b), ((t / kAB) - 1) & 1, abort_flag)) break;
+      tc::fence_after_sync();   // the MMAs that read A / B buffer b have completed
       {
-        // this thread's A row (TMEM lane m), K half h: split and store to TMEM
-        const float* rx = rawX + s * 4096 + 16 * h * 128;
-        float hi[16], lo[16];
+        const float* rx = rawX + s * 4096 + 8 * q * 128;
+        float hi[8], lo[8];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) tc::split_tf32(cok ? rx[k * 128 + m] : 0.f, hi[k], lo[k]);
-        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ACOL + 64 * b + 16 * h);
-        tc::tmem_st16(ta, hi);
-        tc::tmem_st16(ta + 32, lo);
+        for (int k = 0; k < 8; ++k) tc::split_tf32(cok ? rx[k * 128 + m] : 0.f, hi[k], lo[k]);
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ACOL + 64 * b + 8 * q);
+        tc::tmem_st8(ta, hi);
+        tc::tmem_st8(ta + 32, lo);
       }
       // B: chunk (row n, K chunk c), n fastest across the lanes (conflict-free)
       const float2* rp = rawP + s * (kBT / 8);
       const int nval = min(32, cnt - t * 32);
-#pragma unroll 1
       for (int qq = ct; qq < NB * 8; qq += kConv) {
         const int n = qq % NB, c = qq / NB;
         const int chi = n >> 1, im = n & 1;
@@ -487,11 +468,39 @@ k_tc_project_tma(const __grid_constant__ CUtensorMap xmap, int ldx, int nvec,
       tc::fence_before_sync();
       tc::mbar_arrive(empty(s));
       tc::mbar_arrive(afull(b));
-      if (t % kSeg == kSeg - 1 || t == T - 1) {
-        if (!wait_uniform(aempty(b), (t >> 1) & 1, abort_flag)) break;
-        tc::fence_after_sync();
-        flush(t % kSeg == 0 ? 3 : NACC);
+    }
+  } else {
+    // ---- epilogue: C += sum of the segment's three accumulators
+    const int m = 32 * (warp & 3) + lane;
+    const int col = col0 + m;
+    const bool cok = col < ncols && ((col >> 1) % ldx) < nvec;
+    const int ci = col >> 1, sp = ci / ldx, v = ci % ldx;
+    const bool store = (lane & 1) == 0 && cok;
+    const int r0c = atom_c_off[atom];
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int p = sg & 1;
+      if (!wait_uniform(segdone(p), (sg >> 1) & 1, abort_flag)) break;
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int c0 = 0; c0 < NB; c0 += 8) {
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * p + c0);
+        uint32_t a0[8], a1[8];
+        tc::tmem_ld8_nowait(ta + NB, a0);   // hi*hi
+        tc::tmem_ld8_nowait(ta, a1);        // cross terms
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          const float dr = __uint_as_float(a0[j]) + __uint_as_float(a1[j]);
+          const float di = __uint_as_float(a0[j + 1]) + __uint_as_float(a1[j + 1]);
+          const float pr = __shfl_xor_sync(0xffffffffu, dr, 1);   // D[im][2chi]
+          const float pi = __shfl_xor_sync(0xffffffffu, di, 1);   // D[im][2chi+1]
+          const int chi = (c0 + j) >> 1;
+          if (store && chi < npj)
+            atomicAdd(&Cbuf[(size_t)(r0c + 2 * chi + sp) * nvec + v], make_float2(dr + pi, pr - di));
+        }
       }
+      tc::fence_before_sync();
+      tc::mbar_arrive(setfree(p));
     }
   }
   // ---- teardown: after an expired wait, give the copies and MMAs in flight a
@@ -499,7 +508,7 @@ k_tc_project_tma(const __grid_constant__ CUtensorMap xmap, int ldx, int nvec,
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) {
     for (int t = prog[1]; t < prog[0]; ++t) tc::mbar_wait_bounded(full(t % kStages), (t / kStages) & 1);
-    if (prog[2] > 0) tc::mbar_wait_bounded(aempty((prog[2] - 1) & 1), ((prog[2] - 1) >> 1) & 1);
+    if (prog[2] > 0) tc::mbar_wait_bounded(aempty((prog[2] - 1) % kAB), ((prog[2] - 1) / kAB) & 1);
   }
   tc::fence_before_sync();
   __syncthreads();
