@@ -264,11 +264,21 @@ def run_gpu(args):
     flops_launch = flops_per_cell_vector(prob.p, prob.nq, kpt) * prob.ncells * nvec
     clocks = clk.summary()
     peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
+    # DRAM bytes of one hx_local launch: ncu dram__bytes_read + write of the same kernel on the
+    # c1 mesh at 32 vectors (1.364 GB, of which 34 MB fields), scaled by the vector count
+    # (X gather and Y read-modify-write grow with it)
+    if args.config == "c1":
+        traffic = 0.034e9 + (1.364e9 - 0.034e9) * nvec / 32
+        traffic_note = "ncu capture at 32 vectors scaled by vectors; = algorithmic X read + Y RMW"
+    else:
+        traffic, traffic_note = None, "no capture for this configuration"
+
     roofline = {"bound": "alu", "kernel": "hx_local_kernel<float,7,8,k!=0,2> (even-odd sum factorisation)",
                 "achieved": round(flops_launch / (avg_local_ms / 1e3) / 1e12, 3),
                 "peak": round(peak_alu, 2), "unit": "TFLOP/s",
                 "frac": round(flops_launch / (avg_local_ms / 1e3) / 1e12 / peak_alu, 4),
-                "traffic": None,
+                "traffic": traffic,
+                "traffic_note": traffic_note,
                 "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",
                 "flops_per_launch": flops_launch}
 
