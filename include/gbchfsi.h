@@ -288,6 +288,13 @@ gbc_status gbc_apply_h_noalloc(gbc_ctx* ctx, const void* X, void* Y, int nvec, i
 gbc_status gbc_tc_gemm_nt(const float* A, const float* B, float* D, int M, int N, int K,
                           void* stream);
 
+/* Failure-path check of the bounded device waits: one warp waits on an mbarrier
+ * that nothing arrives at, gives up after ``max_iter`` polls (1 .. 2^20) and sets
+ * the device flag that the tensor-core kernels set when a wait expires, so the
+ * next gbc_sync_status returns GBC_ETIMEOUT (and clears it) while the context
+ * stays usable.  Synchronous; GBC_EINVAL for a cap out of range. */
+gbc_status gbc_tc_wait_selftest(int max_iter, void* stream);
+
 /* ---- tracing -------------------------------------------------------------- */
 
 /* Kernel families for gbc_get_timing. */

@@ -795,6 +795,29 @@ cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, co
   return cudaSuccess;
 }
 
+namespace {
+// one warp waits on an mbarrier that nothing arrives at, with the caller's
+// iteration cap, and reports the expiry exactly as the nonlocal kernels do
+__global__ void k_wait_selftest(uint32_t max_iter) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    tc::fence_mbar_init();
+  }
+  __syncwarp();
+  const bool ok = tc::mbar_wait_bounded(tc::smem_u32(&bar), 0, max_iter);
+  if (!ok && threadIdx.x == 0) atomicExch(&g_nltc_err, 1);
+}
+}  // namespace
+
+extern "C" gbc_status gbc_tc_wait_selftest(int max_iter, void* stream) {
+  if (max_iter < 1 || max_iter > (1 << 20)) return GBC_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_wait_selftest<<<1, 32, 0, s>>>((uint32_t)max_iter);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return GBC_ECUDA;
+  return GBC_OK;
+}
+
 // reset / read the bounded-wait flag of the tensor-core nonlocal kernels
 cudaError_t tc_nonlocal_reset(cudaStream_t s) {
   static const int zero = 0;

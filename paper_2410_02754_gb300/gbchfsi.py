@@ -30,7 +30,7 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_apply_h_noalloc", "gbc_batch_create", "gbc_batch_destroy",
            "gbc_batch_last_error", "gbc_batch_filter", "gbc_batch_launches", "gbc_tune",
            "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta",
-           "gbc_tc_gemm_nt", "gbc_set_nonlocal_engine", "gbc_get_nonlocal_engine",
+           "gbc_tc_gemm_nt", "gbc_tc_wait_selftest", "gbc_set_nonlocal_engine", "gbc_get_nonlocal_engine",
            "gbc_sync_status"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH):
         "gbc_energy_grad": ([P, V, DP, V, DP, DP, DP, DP, I, I, V], I),
         "gbc_set_delta": ([P, DP], I),
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
+        "gbc_tc_wait_selftest": ([I, V], I),
         "gbc_set_nonlocal_engine": ([P, I], I),
         "gbc_get_nonlocal_engine": ([P, IP], I),
         "gbc_sync_status": ([P, V], I),
@@ -421,3 +422,10 @@ def tc_gemm_nt(A, B, stream=None):
         raise GbcError(st, "gbc_tc_gemm_nt failed")
     return D
 
+
+
+def tc_wait_selftest(max_iter=1000, stream=None):
+    """Make one bounded device wait expire on purpose (see gbc_tc_wait_selftest)."""
+    st = load_library().gbc_tc_wait_selftest(int(max_iter), _stream_ptr(stream))
+    if st != 0:
+        raise GbcError(st, "gbc_tc_wait_selftest failed")

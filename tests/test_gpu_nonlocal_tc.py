@@ -158,3 +158,30 @@ def test_tensor_nonlocal_long_chains_unbiased(g):
     assert rel(nl, ref) < 3e-6, rel(nl, ref)
     scale = np.real(np.vdot(ref, err)) / np.real(np.vdot(ref, ref))
     assert abs(scale) < 1e-6, scale
+
+
+def test_expired_device_wait_is_reported_and_context_recovers(g):
+    """A bounded wait that runs out (an mbarrier nothing arrives at) is reported by
+    gbc_sync_status as GBC_ETIMEOUT; the flag is then cleared and the tensor-core
+    nonlocal step runs normally again on the same context."""
+    from paper_2410_02754_gb300.gbchfsi import tc_wait_selftest
+    prob = syn.make_problem(ncell=(4, 4, 4), h=(1.0, 1.0, 1.0), p=3, k=(0.1, 0.0, 0.0),
+                            natoms=6, rc=2.0, seed=9, channels=syn.SPD_CHANNELS)
+    X = syn.random_block(prob.nnodes, 32, 4)
+    ref = fe.Discretisation(prob).apply_h(X)
+    ctx = g.Context(0)
+    ctx.set_problem(prob)
+    ctx.set_precision(1)
+    assert ctx.nonlocal_engine() == 1
+    ctx.sync_status()
+    tc_wait_selftest(1000)
+    with pytest.raises(g.GbcError) as err:
+        ctx.sync_status()
+    assert err.value.status == 6   # GBC_ETIMEOUT
+    ctx.sync_status()              # cleared
+    Xd = torch.from_numpy(X).to(torch.complex64).cuda()
+    Yd = torch.empty_like(Xd)
+    ctx.apply_h(Xd, Yd)
+    ctx.sync_status()
+    assert rel(Yd.cpu().numpy().astype(np.complex128), ref) < 1e-5
+    ctx.close()
