@@ -24,6 +24,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -91,7 +92,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples (the summary goes into the JSON line); GBC_CLOCKS_DIR keeps them
+        d = os.environ.get("GBC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"gbc_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:

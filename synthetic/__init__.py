@@ -9,9 +9,10 @@ filter); both the CUDA path and the CPU oracle consume what it produces.
 
 Workload shapes follow the paper's setting (Sec. III.A: hexahedral cells,
 GLL nodes of order p, Gauss quadrature; Sec. II.B, Eq. nlOP: atom-centred
-separable projectors with 2x2 D blocks indexed 2*chi+alpha).  The unstated
-constants (well depth/width, projector Gaussian widths, cut-off radius, B
-magnitude, Delta spread) are the readings recorded in the design doc.
+separable projectors with 2x2 D blocks indexed 2*chi+alpha).  The paper does
+not state the constants (well depth/width, projector Gaussian widths, cut-off
+radius, B magnitude, Delta spread); the defaults of ``make_problem`` are the
+values chosen for them.
 
 Seed streams (offset added to ``seed * 100``): 0 = spinor block X,
 1 = atom positions, 2 = B_xc Fourier modes, 3 = Delta matrices,
