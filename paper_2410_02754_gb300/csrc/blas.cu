@@ -82,8 +82,15 @@ k_gram(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ Yb, const doub
        long long rows, int nvec, int ldx, long long rows_per_chunk, double2* __restrict__ S) {
   __shared__ double2 xs[GT][GT + 1];
   __shared__ double2 ys[GT][GT + 1];
+  // S is Hermitian: only the tiles on and above the diagonal (ti <= tj) are
+  // computed; launch_hermitize mirrors them into the lower triangle
   const int ntile = (nvec + GT - 1) / GT;
-  const int ti = blockIdx.x % ntile, tj = blockIdx.x / ntile;
+  int ti = 0, tj = blockIdx.x;
+  while (tj >= ntile - ti) {
+    tj -= ntile - ti;
+    ++ti;
+  }
+  tj += ti;
   const int i0 = ti * GT, j0 = tj * GT;
   const long long r0 = blockIdx.y * rows_per_chunk;
   const long long r1 = min(rows, r0 + rows_per_chunk);
@@ -382,7 +389,7 @@ cudaError_t launch_gram(const cplx<T>* X, const cplx<T>* Y, const double* md, lo
   cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double2) * (size_t)nvec * nvec, s);
   if (e != cudaSuccess) return e;
   const int ntile = (nvec + GT - 1) / GT;
-  const long long tiles = (long long)ntile * ntile;
+  const long long tiles = (long long)ntile * (ntile + 1) / 2;   // upper-triangle tiles
   // enough row chunks to fill the GPU a few times over
   long long nchunk = (152LL * 8 + tiles - 1) / tiles;
   long long per = (rows + nchunk - 1) / nchunk;

@@ -100,10 +100,9 @@ __global__ void k_hermitize(double2* A, int n) {
     A[(size_t)i * n + i].y = 0.0;
     return;
   }
-  const double2 a = A[(size_t)i * n + j], b = A[(size_t)j * n + i];
-  const double re = 0.5 * (a.x + b.x), im = 0.5 * (a.y - b.y);
-  A[(size_t)i * n + j] = make_double2(re, im);
-  A[(size_t)j * n + i] = make_double2(re, -im);
+  // the Gram kernels compute the upper triangle; the lower one is its mirror
+  const double2 a = A[(size_t)i * n + j];
+  A[(size_t)j * n + i] = make_double2(a.x, -a.y);
 }
 
 // ---- Jacobi --------------------------------------------------------------------

@@ -300,6 +300,7 @@ cudaError_t launch_quad_grad_f32(const gbc_ctx* c, const float2* A, const float2
 gbc_status dense_cholesky_inv_h(gbc_ctx* c, double2* S, int n, double2* Q, cudaStream_t s);
 gbc_status dense_eigh(gbc_ctx* c, double2* A, int n, double* evals_dev, double2* Q,
                       cudaStream_t s);
+// Hermitian matrix from its upper triangle (the lower one mirrored, real diagonal)
 cudaError_t launch_hermitize(double2* A, int n, cudaStream_t s);
 // lanczos helpers
 cudaError_t launch_mdot(const double2* a, const double2* b, const double* md, long long n,
