@@ -293,24 +293,70 @@ gbc_status filter_split_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, int m, doub
 }
 
 // The mixed path keeps complex64 blocks for the filter but runs CholGS and
-// Rayleigh-Ritz on an FP64 copy (FP64 H.X, FP64 Gram, FP64 rotation): an FP32
-// H.X would put a first-order error eps32 * ||H~|| into X^H H X and hence into
-// the Ritz values.  Work slot 4.. holds the FP64 copy.
-struct cholgs_tag {};
-struct rr_tag {};
-template <typename Tag>
-gbc_status promoted(gbc_ctx* c, float2* X, int nvec, int ldx, double* ritz, cudaStream_t s) {
+// CholGS and Rayleigh-Ritz of an FP32 block.  The projected matrices are FP64:
+// S = X^H M_D X accumulates the FP32 entries in FP64 (the same values an FP64
+// copy would give); Rayleigh-Ritz needs an FP64 H.X (an FP32 one would put a
+// first-order error eps32 * ||H~|| into X^H H X and hence into the Ritz values),
+// so it works on an FP64 copy of X (work slot 4).  The rotations X <- X Q act on
+// the FP32 block in float-float arithmetic: the FP64 product rounded to FP32.
+gbc_status rotate_mixed(gbc_ctx* c, float2* X, int nvec, int ldx, const double2* Q, float2* Qsplit,
+                        cudaStream_t s) {
+  const size_t bytes = sizeof(float2) * 2 * (size_t)c->mesh.M * ldx;
+  GBC_TRY(gbc_ensure_work(c, 1, bytes));
+  float2* W = (float2*)c->work[1];
+  {
+    TimerScope ts(c, FAM_ROTATE, s);
+    GBC_CU(c, launch_rotate_ff(X, Q, Qsplit, W, c->mesh.M, nvec, ldx, s));
+  }
+  GBC_CU(c, launch_copy_block<float>(W, X, c->mesh.M, nvec, ldx, s));
+  return GBC_OK;
+}
+
+gbc_status cholgs_mixed(gbc_ctx* c, float2* X, int nvec, int ldx, cudaStream_t s) {
+  const size_t nn = (size_t)nvec * nvec;
+  GBC_TRY(gbc_ensure_work(c, 3, sizeof(double2) * 3 * nn + sizeof(double) * nvec + 256));
+  double2* S = (double2*)c->work[3];
+  double2* Q = S + nn;
+  float2* Qsplit = (float2*)(Q + nn);   // 2 nn float2
+  {
+    TimerScope ts(c, FAM_GRAM, s);
+    GBC_CU(c, launch_gram<float>(X, X, c->d_md, c->mesh.M, nvec, ldx, S, s));
+  }
+  GBC_CU(c, launch_hermitize(S, nvec, s));
+  {
+    TimerScope ts(c, FAM_DENSE, s);
+    GBC_TRY(dense_cholesky_inv_h(c, S, nvec, Q, s));
+  }
+  GBC_TRY(rotate_mixed(c, X, nvec, ldx, Q, Qsplit, s));
+  GBC_CU(c, cudaStreamSynchronize(s));
+  return GBC_OK;
+}
+
+gbc_status rr_mixed(gbc_ctx* c, float2* X, int nvec, int ldx, double* ritz, cudaStream_t s) {
+  const size_t nn = (size_t)nvec * nvec;
   const size_t bytes64 = sizeof(double2) * 2 * (size_t)c->mesh.M * nvec;
   GBC_TRY(gbc_ensure_work(c, 4, bytes64));
+  GBC_TRY(gbc_ensure_work(c, 0, bytes64));
+  GBC_TRY(gbc_ensure_work(c, 3, sizeof(double2) * 3 * nn + sizeof(double) * nvec + 256));
   double2* X64 = (double2*)c->work[4];
+  double2* HX = (double2*)c->work[0];
+  double2* Hp = (double2*)c->work[3];
+  double2* Q = Hp + nn;
+  float2* Qsplit = (float2*)(Q + nn);
+  double* ev = (double*)(Q + 2 * nn);
   GBC_CU(c, launch_convert_block(X, ldx, X64, nvec, c->mesh.M, nvec, s));
-  gbc_status st;
-  if (std::is_same<Tag, cholgs_tag>::value)
-    st = cholgs_t<double>(c, X64, nvec, nvec, s);
-  else
-    st = rr_t<double>(c, X64, nvec, nvec, ritz, s);
-  if (st != GBC_OK) return st;
-  GBC_CU(c, launch_convert_block(X64, nvec, X, ldx, c->mesh.M, nvec, s));
+  GBC_TRY(apply_h_t<double>(c, X64, HX, nvec, nvec, s));
+  {
+    TimerScope ts(c, FAM_GRAM, s);
+    GBC_CU(c, launch_gram<double>(X64, HX, nullptr, c->mesh.M, nvec, nvec, Hp, s));
+  }
+  GBC_CU(c, launch_hermitize(Hp, nvec, s));
+  {
+    TimerScope ts(c, FAM_DENSE, s);
+    GBC_TRY(dense_eigh(c, Hp, nvec, ev, Q, s));
+  }
+  GBC_TRY(rotate_mixed(c, X, nvec, ldx, Q, Qsplit, s));
+  GBC_CU(c, cudaMemcpyAsync(ritz, ev, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
   GBC_CU(c, cudaStreamSynchronize(s));
   return GBC_OK;
 }
@@ -562,7 +608,7 @@ gbc_status gbc_cholgs(gbc_ctx* c, void* X, int nvec, int ldx, void* stream) {
   GBC_TRY(gbc_prepare(c));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->prec == GBC_FP64) return cholgs_t<double>(c, (double2*)X, nvec, ldx, s);
-  return promoted<cholgs_tag>(c, (float2*)X, nvec, ldx, nullptr, s);
+  return cholgs_mixed(c, (float2*)X, nvec, ldx, s);
 }
 
 gbc_status gbc_rayleigh_ritz(gbc_ctx* c, void* X, int nvec, int ldx, double* ritz, void* stream) {
@@ -573,7 +619,7 @@ gbc_status gbc_rayleigh_ritz(gbc_ctx* c, void* X, int nvec, int ldx, double* rit
   GBC_TRY(gbc_prepare(c));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->prec == GBC_FP64) return rr_t<double>(c, (double2*)X, nvec, ldx, ritz, s);
-  return promoted<rr_tag>(c, (float2*)X, nvec, ldx, ritz, s);
+  return rr_mixed(c, (float2*)X, nvec, ldx, ritz, s);
 }
 
 gbc_status gbc_lanczos_bounds(gbc_ctx* c, const void* v0, int steps, double* lmin, double* lmax,

@@ -401,12 +401,122 @@ cudaError_t launch_gram(const cplx<T>* X, const cplx<T>* Y, const double* md, lo
   return cudaGetLastError();
 }
 
+// Out[row][j] = sum_i X[row][i] Q[i][j] for an FP32 block X and an FP64 Q given as
+// Q = Qh + Ql (FP32 pairs), accumulated in two-FP32 (float-float) arithmetic on
+// the FP32 pipes and rounded to FP32 once: the result of an FP64 product rounded
+// to FP32, at several times the FP64 rate.  Per real product x*q: the rounded
+// product and its exact error (FMA), a TwoSum into the high word, the error
+// terms and x*Ql into the low word.  Intrinsics keep every step uncontracted.
+__device__ __forceinline__ void ff_mac(float& sh, float& sl, float x, float qh, float ql) {
+  const float p = __fmul_rn(x, qh);
+  const float pe = __fmaf_rn(x, qh, -p);                   // x*qh - p, exact
+  const float t = __fadd_rn(sh, p);                        // TwoSum(sh, p)
+  const float bb = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  sh = t;
+  sl = __fmaf_rn(x, ql, __fadd_rn(sl, __fadd_rn(err, pe)));
+}
+
+__global__ void __launch_bounds__(256)
+k_rotate_ff(const float2* __restrict__ X, const float2* __restrict__ Qh,
+            const float2* __restrict__ Ql, float2* __restrict__ Out, long long rows, int nvec,
+            int ldx) {
+  __shared__ float2 xs[RT][KT + 1];
+  __shared__ float2 qhs[KT][RT + 1];
+  __shared__ float2 qls[KT][RT + 1];
+  const int ntj = (nvec + RT - 1) / RT;
+  const long long r0 = (long long)(blockIdx.x / ntj) * RT;
+  const int j0 = (blockIdx.x % ntj) * RT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float2 ah[4][4], al[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      ah[a][b] = make_float2(0.f, 0.f);
+      al[a][b] = make_float2(0.f, 0.f);
+    }
+  for (int k0 = 0; k0 < nvec; k0 += KT) {
+    for (int t = threadIdx.x; t < RT * KT; t += 256) {
+      const int rr = t / KT, kk = t % KT;
+      const long long r = r0 + rr;
+      float2 v = make_float2(0.f, 0.f);
+      if (r < rows && k0 + kk < nvec) v = X[r * ldx + k0 + kk];
+      xs[rr][kk] = v;
+    }
+    for (int t = threadIdx.x; t < KT * RT; t += 256) {
+      const int kk = t / RT, jj = t % RT;
+      float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+      if (k0 + kk < nvec && j0 + jj < nvec) {
+        h = Qh[(size_t)(k0 + kk) * nvec + j0 + jj];
+        l = Ql[(size_t)(k0 + kk) * nvec + j0 + jj];
+      }
+      qhs[kk][jj] = h;
+      qls[kk][jj] = l;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < KT; ++kk) {
+      float2 xv[4], hv[4], lv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xv[a] = xs[ty + 16 * a][kk];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        hv[b] = qhs[kk][tx + 16 * b];
+        lv[b] = qls[kk][tx + 16 * b];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          // (x.re + i x.im)(q.re + i q.im)
+          ff_mac(ah[a][b].x, al[a][b].x, xv[a].x, hv[b].x, lv[b].x);
+          ff_mac(ah[a][b].x, al[a][b].x, -xv[a].y, hv[b].y, lv[b].y);
+          ff_mac(ah[a][b].y, al[a][b].y, xv[a].x, hv[b].y, lv[b].y);
+          ff_mac(ah[a][b].y, al[a][b].y, xv[a].y, hv[b].x, lv[b].x);
+        }
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 4; ++a) {
+    const long long r = r0 + ty + 16 * a;
+    if (r >= rows) continue;
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx + 16 * b;
+      if (j < nvec)
+        Out[r * ldx + j] = make_float2(__fadd_rn(ah[a][b].x, al[a][b].x),
+                                       __fadd_rn(ah[a][b].y, al[a][b].y));
+    }
+  }
+}
+
+// Q (FP64, n x n) -> Qh = fl32(Q), Ql = fl32(Q - Qh)
+__global__ void k_split_q(const double2* __restrict__ Q, float2* __restrict__ Qh,
+                          float2* __restrict__ Ql, long long n2) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n2) return;
+  const double2 q = Q[t];
+  const float hx = (float)q.x, hy = (float)q.y;
+  Qh[t] = make_float2(hx, hy);
+  Ql[t] = make_float2((float)(q.x - (double)hx), (float)(q.y - (double)hy));
+}
+
 template <typename T>
 cudaError_t launch_rotate(const cplx<T>* X, const double2* Q, cplx<T>* Out, long long M, int nvec,
                           int ldx, cudaStream_t s) {
   const long long rows = 2 * M;
   const long long nb = ((rows + RT - 1) / RT) * ((nvec + RT - 1) / RT);
   k_rotate<T><<<(unsigned)nb, 256, 0, s>>>(X, Q, Out, rows, nvec, ldx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_ff(const float2* X, const double2* Q, float2* Qsplit, float2* Out,
+                             long long M, int nvec, int ldx, cudaStream_t s) {
+  const long long n2 = (long long)nvec * nvec;
+  k_split_q<<<grid_for(n2), 256, 0, s>>>(Q, Qsplit, Qsplit + n2, n2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long rows = 2 * M;
+  const long long nb = ((rows + RT - 1) / RT) * ((nvec + RT - 1) / RT);
+  k_rotate_ff<<<(unsigned)nb, 256, 0, s>>>(X, Qsplit, Qsplit + n2, Out, rows, nvec, ldx);
   return cudaGetLastError();
 }
 

@@ -300,6 +300,10 @@ cudaError_t launch_quad_grad_f32(const gbc_ctx* c, const float2* A, const float2
 gbc_status dense_cholesky_inv_h(gbc_ctx* c, double2* S, int n, double2* Q, cudaStream_t s);
 gbc_status dense_eigh(gbc_ctx* c, double2* A, int n, double* evals_dev, double2* Q,
                       cudaStream_t s);
+// Out = X Q for an FP32 block and an FP64 Q in float-float arithmetic (FP64-accurate,
+// rounded to FP32); Qsplit: 2 n^2 float2 scratch
+cudaError_t launch_rotate_ff(const float2* X, const double2* Q, float2* Qsplit, float2* Out,
+                             long long M, int nvec, int ldx, cudaStream_t s);
 // Hermitian matrix from its upper triangle (the lower one mirrored, real diagonal)
 cudaError_t launch_hermitize(double2* A, int n, cudaStream_t s);
 // lanczos helpers
