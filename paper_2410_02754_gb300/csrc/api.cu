@@ -293,12 +293,13 @@ gbc_status filter_split_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, int m, doub
 }
 
 // The mixed path keeps complex64 blocks for the filter but runs CholGS and
-// CholGS and Rayleigh-Ritz of an FP32 block.  The projected matrices are FP64:
-// S = X^H M_D X accumulates the FP32 entries in FP64 (the same values an FP64
-// copy would give); Rayleigh-Ritz needs an FP64 H.X (an FP32 one would put a
-// first-order error eps32 * ||H~|| into X^H H X and hence into the Ritz values),
-// so it works on an FP64 copy of X (work slot 4).  The rotations X <- X Q act on
-// the FP32 block in float-float arithmetic: the FP64 product rounded to FP32.
+// CholGS and Rayleigh-Ritz of an FP32 block.  The projected matrices are FP64-
+// accurate: S = X^H M_D X and Hp = X^H (H X) are accumulated in float-float
+// arithmetic on the FP32 pipes; Rayleigh-Ritz needs an FP64 H.X (an FP32 one
+// would put a first-order error eps32 * ||H~|| into X^H H X and hence into the
+// Ritz values), computed on an FP64 copy of X (work slot 4).  The rotations
+// X <- X Q act on the FP32 block in float-float arithmetic as well: the FP64
+// product rounded to FP32.
 gbc_status rotate_mixed(gbc_ctx* c, float2* X, int nvec, int ldx, const double2* Q, float2* Qsplit,
                         cudaStream_t s) {
   const size_t bytes = sizeof(float2) * 2 * (size_t)c->mesh.M * ldx;
@@ -320,7 +321,7 @@ gbc_status cholgs_mixed(gbc_ctx* c, float2* X, int nvec, int ldx, cudaStream_t s
   float2* Qsplit = (float2*)(Q + nn);   // 2 nn float2
   {
     TimerScope ts(c, FAM_GRAM, s);
-    GBC_CU(c, launch_gram<float>(X, X, c->d_md, c->mesh.M, nvec, ldx, S, s));
+    GBC_CU(c, launch_gram_ff<float>(X, ldx, X, ldx, c->d_md, c->mesh.M, nvec, S, s));
   }
   GBC_CU(c, launch_hermitize(S, nvec, s));
   {
@@ -348,7 +349,7 @@ gbc_status rr_mixed(gbc_ctx* c, float2* X, int nvec, int ldx, double* ritz, cuda
   GBC_TRY(apply_h_t<double>(c, X64, HX, nvec, nvec, s));
   {
     TimerScope ts(c, FAM_GRAM, s);
-    GBC_CU(c, launch_gram<double>(X64, HX, nullptr, c->mesh.M, nvec, nvec, Hp, s));
+    GBC_CU(c, launch_gram_ff<double>(X, ldx, HX, nvec, nullptr, c->mesh.M, nvec, Hp, s));
   }
   GBC_CU(c, launch_hermitize(Hp, nvec, s));
   {

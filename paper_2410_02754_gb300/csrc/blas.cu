@@ -144,6 +144,112 @@ k_gram(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ Yb, const doub
     }
 }
 
+// S = X^H diag(w) Y (Hermitian, upper-triangle tiles as k_gram) for an FP32 block
+// X and Y either the same FP32 block (w = M_D: CholGS) or an FP64 block (w = 1:
+// Rayleigh-Ritz with Y = H X), in float-float arithmetic on the FP32 pipes.  The
+// X side carries the weight as a two-FP32 value (x*wh exact by FMA, + x*wl), an
+// FP64 Y entry is split into two FP32 words on load; per real product the rounded
+// product of the high words and its exact error, plus the two cross terms, are
+// TwoSum-accumulated into (hi, lo), and each CTA adds hi + lo to S in FP64.
+__device__ __forceinline__ void ff_acc(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = __fmaf_rn(ah, bh, -p);                  // ah*bh - p, exact
+  const float small = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+  const float t = __fadd_rn(sh, p);                        // TwoSum(sh, p)
+  const float bb = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, __fadd_rn(pe, small)));
+}
+
+template <typename TY>
+__global__ void __launch_bounds__(256)
+k_gram_ff(const float2* __restrict__ X, int ldx, const cplx<TY>* __restrict__ Yb, int ldy,
+          const double* __restrict__ md, long long rows, int nvec, long long rows_per_chunk,
+          double2* __restrict__ S) {
+  __shared__ float2 xh[GT][GT + 1], xl[GT][GT + 1];
+  __shared__ float2 yh[GT][GT + 1], yl[GT][GT + 1];
+  const int ntile = (nvec + GT - 1) / GT;
+  int ti = 0, tj = blockIdx.x;
+  while (tj >= ntile - ti) {
+    tj -= ntile - ti;
+    ++ti;
+  }
+  tj += ti;
+  const int i0 = ti * GT, j0 = tj * GT;
+  const long long r0 = blockIdx.y * rows_per_chunk;
+  const long long r1 = min(rows, r0 + rows_per_chunk);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float ah[2][2][2], al[2][2][2];   // [a][b][re / im]
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int q = 0; q < 2; ++q) ah[a][b][q] = al[a][b][q] = 0.f;
+  for (long long rb = r0; rb < r1; rb += GT) {
+    for (int t = threadIdx.x; t < GT * GT; t += 256) {
+      const int rr = t / GT, cc = t % GT;
+      const long long r = rb + rr;
+      float2 vh = make_float2(0.f, 0.f), vl = vh, uh = vh, ul = vh;
+      if (r < r1) {
+        if (i0 + cc < nvec) {
+          const float2 x = X[r * ldx + i0 + cc];
+          if (md) {
+            const double w = md[r >> 1];
+            const float wh = (float)w, wl = (float)(w - (double)wh);
+            const float ph = __fmul_rn(x.x, wh), qh = __fmul_rn(x.y, wh);
+            vh = make_float2(ph, qh);
+            vl = make_float2(__fmaf_rn(x.x, wl, __fmaf_rn(x.x, wh, -ph)),
+                             __fmaf_rn(x.y, wl, __fmaf_rn(x.y, wh, -qh)));
+          } else {
+            vh = x;
+          }
+        }
+        if (j0 + cc < nvec) {
+          const cplx<TY> y = Yb[r * ldy + j0 + cc];
+          const float hx = (float)y.x, hy = (float)y.y;
+          uh = make_float2(hx, hy);
+          ul = make_float2((float)((double)y.x - (double)hx), (float)((double)y.y - (double)hy));
+        }
+      }
+      xh[rr][cc] = vh;
+      xl[rr][cc] = vl;
+      yh[rr][cc] = uh;
+      yl[rr][cc] = ul;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int rr = 0; rr < GT; ++rr) {
+      float2 xa[2], xb[2], ya[2], yb[2];
+      xa[0] = xh[rr][2 * tx];
+      xa[1] = xh[rr][2 * tx + 1];
+      xb[0] = xl[rr][2 * tx];
+      xb[1] = xl[rr][2 * tx + 1];
+      ya[0] = yh[rr][2 * ty];
+      ya[1] = yh[rr][2 * ty + 1];
+      yb[0] = yl[rr][2 * ty];
+      yb[1] = yl[rr][2 * ty + 1];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          // conj(x) * y: re = xr yr + xi yi, im = xr yi - xi yr
+          ff_acc(ah[a][b][0], al[a][b][0], xa[a].x, xb[a].x, ya[b].x, yb[b].x);
+          ff_acc(ah[a][b][0], al[a][b][0], xa[a].y, xb[a].y, ya[b].y, yb[b].y);
+          ff_acc(ah[a][b][1], al[a][b][1], xa[a].x, xb[a].x, ya[b].y, yb[b].y);
+          ff_acc(ah[a][b][1], al[a][b][1], -xa[a].y, -xb[a].y, ya[b].x, yb[b].x);
+        }
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + 2 * tx + a, j = j0 + 2 * ty + b;
+      if (i < nvec && j < nvec) {
+        atomicAdd(&S[(size_t)i * nvec + j].x, (double)ah[a][b][0] + (double)al[a][b][0]);
+        atomicAdd(&S[(size_t)i * nvec + j].y, (double)ah[a][b][1] + (double)al[a][b][1]);
+      }
+    }
+}
+
 // Out[row][j] = sum_i X[row][i] Q[i][j]; 64 x 64 output tile, K-steps of 16.
 constexpr int RT = 64, KT = 16;
 template <typename T>
@@ -507,6 +613,28 @@ cudaError_t launch_rotate(const cplx<T>* X, const double2* Q, cplx<T>* Out, long
   k_rotate<T><<<(unsigned)nb, 256, 0, s>>>(X, Q, Out, rows, nvec, ldx);
   return cudaGetLastError();
 }
+
+template <typename TY>
+cudaError_t launch_gram_ff(const float2* X, int ldx, const cplx<TY>* Y, int ldy, const double* md,
+                           long long M, int nvec, double2* S, cudaStream_t s) {
+  const long long rows = 2 * M;
+  cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double2) * (size_t)nvec * nvec, s);
+  if (e != cudaSuccess) return e;
+  const int ntile = (nvec + GT - 1) / GT;
+  const long long tiles = (long long)ntile * (ntile + 1) / 2;   // upper-triangle tiles
+  long long nchunk = (152LL * 8 + tiles - 1) / tiles;
+  long long per = (rows + nchunk - 1) / nchunk;
+  per = ((per + GT - 1) / GT) * GT;
+  if (per < GT) per = GT;
+  nchunk = (rows + per - 1) / per;
+  dim3 grid((unsigned)tiles, (unsigned)nchunk);
+  k_gram_ff<TY><<<grid, 256, 0, s>>>(X, ldx, Y, ldy, md, rows, nvec, per, S);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gram_ff<float>(const float2*, int, const float2*, int, const double*,
+                                           long long, int, double2*, cudaStream_t);
+template cudaError_t launch_gram_ff<double>(const float2*, int, const double2*, int, const double*,
+                                            long long, int, double2*, cudaStream_t);
 
 cudaError_t launch_rotate_ff(const float2* X, const double2* Q, float2* Qsplit, float2* Out,
                              long long M, int nvec, int ldx, cudaStream_t s) {

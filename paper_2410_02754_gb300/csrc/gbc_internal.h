@@ -300,6 +300,11 @@ cudaError_t launch_quad_grad_f32(const gbc_ctx* c, const float2* A, const float2
 gbc_status dense_cholesky_inv_h(gbc_ctx* c, double2* S, int n, double2* Q, cudaStream_t s);
 gbc_status dense_eigh(gbc_ctx* c, double2* A, int n, double* evals_dev, double2* Q,
                       cudaStream_t s);
+// S = X^H diag(w) Y (upper-triangle tiles, FP64 result) for an FP32 block X and an FP32
+// (w = md) or FP64 (md = null) block Y, in float-float arithmetic on the FP32 pipes
+template <typename TY>
+cudaError_t launch_gram_ff(const float2* X, int ldx, const cplx<TY>* Y, int ldy, const double* md,
+                           long long M, int nvec, double2* S, cudaStream_t s);
 // Out = X Q for an FP32 block and an FP64 Q in float-float arithmetic (FP64-accurate,
 // rounded to FP32); Qsplit: 2 n^2 float2 scratch
 cudaError_t launch_rotate_ff(const float2* X, const double2* Q, float2* Qsplit, float2* Out,
