@@ -459,6 +459,86 @@ def run_batch(args):
         print(json.dumps(out), flush=True)
 
 
+def run_backward(args):
+    """Config 3: the c1 mesh and atoms at the Gamma point, 128 vectors, degree 20: one
+    step = FP32 forward filter + energy gradient (G_Y = 2 H Y W) + the backward of the
+    filter (gbc_filter_vjp, checkpoints every 5 degrees) giving dL/dX, dL/dV_eff,
+    dL/dB_xc at the quadrature points and dL/dDelta."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import synthetic as syn
+    import paper_2410_02754_gb300 as g
+
+    rank, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "gloo")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    ge.build()
+    cfg = syn.CONFIGS["c3"]
+    nvec = args.nvec or cfg["nvec"]
+    degree = args.degree or cfg["degree"]
+    prob = syn.config("c3", seed=0)
+    M = prob.nnodes
+    c = g.Context(torch.cuda.current_device())
+    c.set_problem(prob)
+    c.set_precision(g.FP32)
+    c.set_nonlocal_engine(args.nl_engine)
+    lo, hi = c.lanczos_bounds(torch.from_numpy(syn.random_start(M, 0)).cuda(), cfg["lanczos"])
+    X0 = torch.from_numpy(syn.random_block(M, nvec, 0)).to(torch.complex64).cuda()
+    c.cholgs(X0)
+    ritz = c.rayleigh_ritz(X0)
+    lT, lmin = float(ritz[-1]), min(lo, float(ritz[0]))
+    w = np.random.default_rng(5).uniform(0.0, 1.0, nvec)
+    X = torch.empty_like(X0)
+    GY = torch.empty_like(X0)
+    GX = torch.empty_like(X0)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        X.copy_(X0)
+        c.filter(X, degree, lT, hi, lmin)
+        if ev:
+            ev[0].record(stream)
+        c.energy_grad(X, w, GY)
+        c.filter_vjp(X0, GY, GX, degree, lT, hi, lmin, ckpt_every=5)
+        if ev:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist_barrier()
+    t_fwd, t_bwd = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            step((e1, e2))
+            torch.cuda.synchronize()
+            t_fwd.append(e0.elapsed_time(e1))
+            t_bwd.append(e1.elapsed_time(e2))
+    ms_fwd, ms_bwd = float(np.mean(t_fwd)), float(np.mean(t_bwd))
+    ms = dist_max(ms_fwd + ms_bwd, "cuda" if world > 1 else "cpu")
+    units = M * nvec * degree
+    out = {"metric": "ChFSI filter forward + backward spinor-DOF\u00b7vectors\u00b7degree/s, 1 GB300",
+           "value": dist_sum(units, "cuda" if world > 1 else "cpu") / (ms / 1e3), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": f"16x16x16 periodic cells, p=6, nq=8 ({M:,} nodes), 64 atoms x 18 "
+                                  f"SOC projectors, {nvec} vectors, degree {degree}, Gamma point; "
+                                  "L = sum_i w_i y_i^H H y_i",
+                      "config": "c3", "checkpoint_every": 5},
+           "ms_forward_filter": ms_fwd, "ms_backward": ms_bwd,
+           "backward_over_forward": ms_bwd / ms_fwd,
+           "backward_note": "energy gradient + filter VJP, gradients copied to the host",
+           "clocks": clk.summary()}
+    c.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def cpu_sample(args, prob, k, budget_s=20.0, nv=2):
     """One recurrence step (H.X by element-by-element quadrature + the sigma-scaled
     update) of the FP64 oracle on an nv-vector sample of the workload."""
@@ -538,6 +618,8 @@ def main():
         run_reference(args)
     elif args.config == "c2":
         run_batch(args)
+    elif args.config == "c3":
+        run_backward(args)
     else:
         run_gpu(args)
 
