@@ -18,9 +18,12 @@ What it computes (each function cites the passage it follows):
                  the residual-split form of the filter, dense brute force.
 * ``grad``    -- reverse-mode gradients of L = sum_i w_i y_i^H H y_i through
                  the filter.
+* ``density`` -- electron density rho and magnetisation density m at the Gauss
+                 points from an occupied spinor block (Eqs. rho, mag).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests in
-``tests/test_oracle_pins.py`` except the residual-split reformulation's
+``tests/test_oracle_pins.py``, ``tests/test_oracle_grad.py`` and
+``tests/test_oracle_density.py`` except the residual-split reformulation's
 relation to the authors' unpublished variant ("parity unpinned" for that
 relation only; its exact equality with the direct filter is pinned).
 """
