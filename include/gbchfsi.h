@@ -215,6 +215,31 @@ gbc_status gbc_energy_grad(gbc_ctx* ctx, const void* Y, const double* w, void* G
  * gbc_set_projectors; layout as there).  Synchronous. */
 gbc_status gbc_set_delta(gbc_ctx* ctx, const double* delta);
 
+/* ---- densities (Sec. II, Eqs. rho and mag) ------------------------------------- */
+
+/* Electron density rho(r_q) = sum_n f_n psi_n^H psi_n and magnetisation density
+ * m(r_q) = sum_n f_n psi_n^H sigma psi_n at every Gauss point r_q of every cell,
+ * psi_n(r) = sum_I N_I(r) X[I][.][n] (Eq. FEWfns; X holds the periodic part of a
+ * Bloch spinor, whose phase cancels).  Per component: rho = |u|^2 + |d|^2,
+ * m_x = 2 Re(u* d), m_y = 2 Im(u* d), m_z = |u|^2 - |d|^2 for psi = (u, d).
+ * X: device block [M][2][ldx] in the context precision, columns 0..nvec-1 used;
+ * occ: occupations f_n, nvec doubles (any sign; not normalised).  Products are
+ * formed in the context precision and summed in FP64.  p <= 6
+ * (GBC_EUNSUPPORTED otherwise); GBC_EINVAL for a null pointer or nvec < 1 or
+ * ldx < nvec.
+ *
+ * gbc_density_dev: occ and out are DEVICE arrays; out [E][4][nq^3] doubles
+ * (cell-major; component 0 rho, 1..3 m_x, m_y, m_z; Gauss point q = (qz nq + qy)
+ * nq + qx) is overwritten.  Asynchronous on ``stream``; one kernel launch, and no
+ * allocation once the operator tables are built (see gbc_apply_h_noalloc).
+ * gbc_density: occ, rho and mag are HOST arrays; rho [E][nq^3] and mag
+ * [3][E][nq^3] (layout as gbc_set_fields; mag may be NULL) are written.
+ * Synchronous; uses library workspace. */
+gbc_status gbc_density_dev(gbc_ctx* ctx, const void* X, const double* occ, double* out, int nvec,
+                           int ldx, void* stream);
+gbc_status gbc_density(gbc_ctx* ctx, const void* X, const double* occ, double* rho, double* mag,
+                       int nvec, int ldx, void* stream);
+
 /* ---- batched systems (independent k-points / systems, Sec. III.B) ------------ */
 
 typedef struct gbc_batch gbc_batch;   /* opaque, owned by the library */

@@ -16,21 +16,24 @@ from __future__ import annotations
 import numpy as np
 
 
-def spinor_at_gauss(d, X):
-    """psi[e, q, s, n] = sum_i N_i(r_q) X[I(e, i), s, n], zero for constrained nodes."""
+def spinor_at_gauss(d, X, cells=None):
+    """psi[e, q, s, n] = sum_i N_i(r_q) X[I(e, i), s, n], zero for constrained nodes
+    (all cells, or the listed ones in that order)."""
     mesh, tab = d.mesh, d.tab
     M, _, nv = X.shape
-    Xp = np.concatenate([np.asarray(X, np.complex128), np.zeros((1, 2, nv), np.complex128)])
-    sel = np.where(mesh.cell_nodes >= 0, mesh.cell_nodes, M)      # [E, np^3]
-    # psi[e, q, s, n] = sum_i N3[i, q] Xp[sel[e, i], s, n]
-    return np.einsum("iq,eisn->eqsn", tab.N3, Xp[sel])
+    cn = mesh.cell_nodes if cells is None else mesh.cell_nodes[np.asarray(cells)]
+    sel = np.where(cn >= 0, cn, M)                                 # [E, np^3]
+    vals = np.asarray(X)[np.minimum(sel, M - 1)].astype(np.complex128)
+    vals[sel == M] = 0.0
+    # psi[e, q, s, n] = sum_i N3[i, q] X[sel[e, i], s, n]
+    return np.einsum("iq,eisn->eqsn", tab.N3, vals)
 
 
-def densities(d, X, occ):
+def densities(d, X, occ, cells=None):
     """rho[e, q] and m[3, e, q] (Eqs. rho, mag) for the block X[M][2][nv] with
-    occupations occ[nv]."""
+    occupations occ[nv] (all cells, or the listed ones)."""
     occ = np.asarray(occ, np.float64)
-    psi = spinor_at_gauss(d, X)
+    psi = spinor_at_gauss(d, X, cells)
     u, dn = psi[:, :, 0, :], psi[:, :, 1, :]
     uu = (u.conj() * u).real
     dd = (dn.conj() * dn).real

@@ -292,10 +292,10 @@ cudaError_t launch_copy_block(const cplx<T>* X, cplx<T>* Out, long long M, int n
 // grad_contract.cu : quadrature-point gradient contraction (backward pass)
 cudaError_t launch_quad_grad_f64(const gbc_ctx* c, const double2* A, const double2* B,
                                  const double* wv, double scale, int nvec, int ldx, double* g,
-                                 cudaStream_t s);
+                                 int pointwise, cudaStream_t s);
 cudaError_t launch_quad_grad_f32(const gbc_ctx* c, const float2* A, const float2* B,
                                  const double* wv, double scale, int nvec, int ldx, double* g,
-                                 cudaStream_t s);
+                                 int pointwise, cudaStream_t s);
 // dense.cu : small dense FP64 linear algebra on the device
 gbc_status dense_cholesky_inv_h(gbc_ctx* c, double2* S, int n, double2* Q, cudaStream_t s);
 gbc_status dense_eigh(gbc_ctx* c, double2* A, int n, double* evals_dev, double2* Q,

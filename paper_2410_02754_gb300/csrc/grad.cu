@@ -119,10 +119,13 @@ namespace {
 
 template <typename T>
 cudaError_t quad_grad(const gbc_ctx* c, const cplx<T>* A, const cplx<T>* B, const double* wv,
-                      double scale, int nvec, int ldx, double* g, cudaStream_t s) {
+                      double scale, int nvec, int ldx, double* g, cudaStream_t s,
+                      int pointwise = 0) {
   if (std::is_same<T, double>::value)
-    return launch_quad_grad_f64(c, (const double2*)A, (const double2*)B, wv, scale, nvec, ldx, g, s);
-  return launch_quad_grad_f32(c, (const float2*)A, (const float2*)B, wv, scale, nvec, ldx, g, s);
+    return launch_quad_grad_f64(c, (const double2*)A, (const double2*)B, wv, scale, nvec, ldx, g,
+                                pointwise, s);
+  return launch_quad_grad_f32(c, (const float2*)A, (const float2*)B, wv, scale, nvec, ldx, g,
+                              pointwise, s);
 }
 
 // projector-coefficient outer products for the Delta gradient
@@ -180,12 +183,26 @@ gbc_status grad_scratch(gbc_ctx* c, int nvec, GradScratch* gs) {
   return GBC_OK;
 }
 
-// copy g [E][4][q] to the four host arrays and the Hermitian-projected gD to host
-gbc_status grad_download(gbc_ctx* c, const GradScratch& gs, double* gV, double* gB, double* gDelta,
-                         cudaStream_t s) {
+// copy g [E][4][q] (device) to the host arrays g0 [E][q] and g13 [3][E][q]
+// (either may be null).  Synchronous.
+gbc_status download_quad(gbc_ctx* c, const double* g, double* g0, double* g13, cudaStream_t s) {
   const size_t nq3 = (size_t)c->nq * c->nq * c->nq;
   const size_t E = (size_t)c->mesh.E;
   std::vector<double> h(E * 4 * nq3);
+  GBC_CU(c, cudaMemcpyAsync(h.data(), g, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  GBC_CU(c, cudaStreamSynchronize(s));
+  for (size_t e = 0; e < E; ++e)
+    for (int comp = 0; comp < 4; ++comp) {
+      double* dst = comp == 0 ? g0 : (g13 ? g13 + (size_t)(comp - 1) * E * nq3 : nullptr);
+      if (!dst) continue;
+      std::copy(&h[(e * 4 + comp) * nq3], &h[(e * 4 + comp) * nq3] + nq3, dst + e * nq3);
+    }
+  return GBC_OK;
+}
+
+// copy g [E][4][q] to the four host arrays and the Hermitian-projected gD to host
+gbc_status grad_download(gbc_ctx* c, const GradScratch& gs, double* gV, double* gB, double* gDelta,
+                         cudaStream_t s) {
   const ProjDev& pj = c->proj;
   if (pj.natoms) {
     dim3 grid(pj.natoms, 2 * pj.max_npj);
@@ -195,15 +212,7 @@ gbc_status grad_download(gbc_ctx* c, const GradScratch& gs, double* gV, double* 
       GBC_CU(c, cudaMemcpyAsync(gDelta, gs.gD, sizeof(double2) * pj.delta_off[pj.natoms],
                                 cudaMemcpyDeviceToHost, s));
   }
-  GBC_CU(c, cudaMemcpyAsync(h.data(), gs.g, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
-  GBC_CU(c, cudaStreamSynchronize(s));
-  for (size_t e = 0; e < E; ++e)
-    for (int comp = 0; comp < 4; ++comp) {
-      double* dst = comp == 0 ? gV : gB + (size_t)(comp - 1) * E * nq3;
-      if (!dst) continue;
-      std::copy(&h[(e * 4 + comp) * nq3], &h[(e * 4 + comp) * nq3] + nq3, dst + e * nq3);
-    }
-  return GBC_OK;
+  return download_quad(c, gs.g, gV, gB, s);
 }
 
 template <typename T>
@@ -314,9 +323,52 @@ gbc_status energy_grad_t(gbc_ctx* c, const cplx<T>* Y, const double* w, cplx<T>*
   return GBC_OK;
 }
 
+// rho and m at the Gauss points (Eqs. rho, mag) into out [E][4][nq^3] (device)
+template <typename T>
+cudaError_t density_t(const gbc_ctx* c, const cplx<T>* X, const double* occ_dev, double* out,
+                      int nvec, int ldx, cudaStream_t s) {
+  return quad_grad<T>(c, X, X, occ_dev, 1.0, nvec, ldx, out, s, 1);
+}
+
+gbc_status density_check(gbc_ctx* c, const void* X, const double* occ, const double* out, int nvec,
+                         int ldx) {
+  if (!X || !occ || !out) return gbc_fail(c, GBC_EINVAL, "null argument");
+  if (nvec < 1 || ldx < nvec) return gbc_fail(c, GBC_EINVAL, "need 1 <= nvec <= ldx");
+  GBC_TRY(gbc_prepare(c));
+  if (c->mesh.p > 6) return gbc_fail(c, GBC_EUNSUPPORTED, "densities support p <= 6");
+  return GBC_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+gbc_status gbc_density_dev(gbc_ctx* c, const void* X, const double* occ, double* out, int nvec,
+                           int ldx, void* stream) {
+  if (!c) return GBC_EINVAL;
+  GBC_TRY(density_check(c, X, occ, out, nvec, ldx));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->prec == GBC_FP64)
+    GBC_CU(c, density_t<double>(c, (const double2*)X, occ, out, nvec, ldx, s));
+  else
+    GBC_CU(c, density_t<float>(c, (const float2*)X, occ, out, nvec, ldx, s));
+  return GBC_OK;
+}
+
+gbc_status gbc_density(gbc_ctx* c, const void* X, const double* occ, double* rho, double* mag,
+                       int nvec, int ldx, void* stream) {
+  if (!c) return GBC_EINVAL;
+  GBC_TRY(density_check(c, X, occ, rho, nvec, ldx));
+  cudaStream_t s = (cudaStream_t)stream;
+  GradScratch gs;
+  GBC_TRY(grad_scratch(c, nvec, &gs));
+  GBC_CU(c, cudaMemcpyAsync(gs.wv, occ, sizeof(double) * nvec, cudaMemcpyHostToDevice, s));
+  if (c->prec == GBC_FP64)
+    GBC_CU(c, density_t<double>(c, (const double2*)X, gs.wv, gs.g, nvec, ldx, s));
+  else
+    GBC_CU(c, density_t<float>(c, (const float2*)X, gs.wv, gs.g, nvec, ldx, s));
+  return download_quad(c, gs.g, rho, mag, s);
+}
 
 gbc_status gbc_filter_vjp(gbc_ctx* c, const void* X0, const void* GY, void* GX, double* gV,
                           double* gB, double* gDelta, int nvec, int ldx, int degree, double lT,

@@ -8,6 +8,10 @@
 // sigma^d, Eq. FEHloc).  These are the density / magnetisation-density
 // contractions of Eqs. rho and mag with the adjoint as the bra.
 //
+// Point-wise mode (A = B, wv = occupations): g[e][c][q] = scale * sum_v wv[v]
+// Re(a_v^H S_c a_v), written rather than accumulated and without w_q J, is
+// (rho, m_x, m_y, m_z) at the Gauss points (Eqs. rho, mag).
+//
 // One CTA owns one cell and walks all vectors in chunks of VB, so every g[e]
 // row is written by exactly one CTA (no atomics).  Interpolation to the Gauss
 // points is sum-factorised as in the cell apply (3 one-dimensional stages);
@@ -27,6 +31,7 @@ template <typename T> struct GradArgs {
   int ldx, nvec;
   double scale;
   MeshDev mesh;
+  int pointwise;       // 1: g = scale * sum (no w_q J, overwrite)
 };
 
 template <typename T, int NP, int NQ> struct InterpTab {
@@ -139,6 +144,13 @@ quad_grad_kernel(const GradArgs<T> a, const InterpTab<T, NP, NQ> tb) {
     C ua[2][NQ], ub[2][NQ];
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
+      if (which == 1 && a.A == a.B) {   // a^H S a: one interpolation serves both sides
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) ub[s][q] = ua[s][q];
+        continue;
+      }
       const cplx<T>* src = which == 0 ? a.A : a.B;
       for (int i = lane; i < NP * NP * NP; i += TPV) {
         const int ix = i % NP, iy = (i / NP) % NP, iz = i / (NP * NP);
@@ -193,8 +205,13 @@ quad_grad_kernel(const GradArgs<T> a, const InterpTab<T, NP, NQ> tb) {
         double sum = 0.0;
         for (int w = 0; w < VB; ++w) sum += red[((w * 64 + lane) * 4 + c) * NQ + qz];
         const int q = (qz * NQ + y) * NQ + x;
-        const double wq = tb.wq[x] * tb.wq[y] * tb.wq[qz] * tb.jac;
-        a.g[((size_t)e * 4 + c) * NQ * NQ * NQ + q] += a.scale * wq * sum;
+        double* dst = &a.g[((size_t)e * 4 + c) * NQ * NQ * NQ + q];
+        if (a.pointwise) {
+          *dst = a.scale * sum;
+        } else {
+          const double wq = tb.wq[x] * tb.wq[y] * tb.wq[qz] * tb.jac;
+          *dst += a.scale * wq * sum;
+        }
       }
   }
 }
@@ -208,9 +225,9 @@ template <typename T, int NP, int NQ, int VB> constexpr size_t quad_grad_smem() 
 template <typename T, int NP, int VB>
 cudaError_t launch_quad_grad_p(const gbc_ctx* c, const cplx<T>* A, const cplx<T>* B,
                                const double* wv, double scale, int nvec, int ldx, double* g,
-                               cudaStream_t s) {
+                               int pointwise, cudaStream_t s) {
   constexpr int NQ = NP + 1;
-  GradArgs<T> a{A, B, wv, g, ldx, nvec, scale, c->mesh};
+  GradArgs<T> a{A, B, wv, g, ldx, nvec, scale, c->mesh, pointwise};
   InterpTab<T, NP, NQ> tb;
   for (int i = 0; i < NP; ++i)
     for (int q = 0; q < NQ; ++q) tb.N[i][q] = (T)c->tab.N1[i * NQ + q];
@@ -228,14 +245,14 @@ cudaError_t launch_quad_grad_p(const gbc_ctx* c, const cplx<T>* A, const cplx<T>
 template <typename T, int VB>
 cudaError_t launch_quad_grad_t(const gbc_ctx* c, const cplx<T>* A, const cplx<T>* B,
                                const double* wv, double scale, int nvec, int ldx, double* g,
-                               cudaStream_t s) {
+                               int pointwise, cudaStream_t s) {
   switch (c->mesh.p) {
-    case 2: return launch_quad_grad_p<T, 3, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
-    case 3: return launch_quad_grad_p<T, 4, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
-    case 4: return launch_quad_grad_p<T, 5, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
-    case 5: return launch_quad_grad_p<T, 6, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
-    case 6: return launch_quad_grad_p<T, 7, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
-    case 7: return launch_quad_grad_p<T, 8, VB>(c, A, B, wv, scale, nvec, ldx, g, s);
+    case 2: return launch_quad_grad_p<T, 3, VB>(c, A, B, wv, scale, nvec, ldx, g, pointwise, s);
+    case 3: return launch_quad_grad_p<T, 4, VB>(c, A, B, wv, scale, nvec, ldx, g, pointwise, s);
+    case 4: return launch_quad_grad_p<T, 5, VB>(c, A, B, wv, scale, nvec, ldx, g, pointwise, s);
+    case 5: return launch_quad_grad_p<T, 6, VB>(c, A, B, wv, scale, nvec, ldx, g, pointwise, s);
+    case 6: return launch_quad_grad_p<T, 7, VB>(c, A, B, wv, scale, nvec, ldx, g, pointwise, s);
+    case 7: return launch_quad_grad_p<T, 8, VB>(c, A, B, wv, scale, nvec, ldx, g, pointwise, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -31,7 +31,7 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_batch_last_error", "gbc_batch_filter", "gbc_batch_launches", "gbc_tune",
            "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta",
            "gbc_tc_gemm_nt", "gbc_tc_wait_selftest", "gbc_set_nonlocal_engine", "gbc_get_nonlocal_engine",
-           "gbc_sync_status"]
+           "gbc_sync_status", "gbc_density", "gbc_density_dev"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -84,6 +84,8 @@ def load_library(path: str = LIB_PATH):
         "gbc_filter_vjp": ([P, V, V, V, DP, DP, DP, I, I, I, D, D, D, I, V], I),
         "gbc_energy_grad": ([P, V, DP, V, DP, DP, DP, DP, I, I, V], I),
         "gbc_set_delta": ([P, DP], I),
+        "gbc_density": ([P, V, DP, DP, DP, I, I, V], I),
+        "gbc_density_dev": ([P, V, V, V, I, I, V], I),
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
         "gbc_tc_wait_selftest": ([I, V], I),
         "gbc_set_nonlocal_engine": ([P, I], I),
@@ -339,6 +341,33 @@ class Context:
         self._chk(self.lib.gbc_energy_grad(self.h, py, wp, pg, ct.byref(loss), dp(gV), dp(gB),
                                            dp(gD), int(nvec), int(ldx), _stream_ptr(stream)))
         return (loss.value,) + self._split(gV, gB, gD)
+
+    def density(self, X, occ, nvec=None, stream=None):
+        """rho and m at the Gauss points (Eqs. rho, mag) of the block X with
+        occupations occ: returns numpy (rho [E, nq^3], m [3, E, nq^3])."""
+        px, ldx = self._block(X)
+        nvec = ldx if nvec is None else nvec
+        _, op = _darr(np.asarray(occ, np.float64)[:nvec])
+        n = self.ncells * self.nq ** 3
+        rho, mag = np.zeros(n), np.zeros(3 * n)
+        dp = lambda a: a.ctypes.data_as(ct.POINTER(ct.c_double))
+        self._chk(self.lib.gbc_density(self.h, px, op, dp(rho), dp(mag), int(nvec), int(ldx),
+                                       _stream_ptr(stream)))
+        return rho.reshape(self.ncells, -1), mag.reshape(3, self.ncells, -1)
+
+    def density_dev(self, X, occ, out, nvec=None, stream=None):
+        """Device form: occ (float64 CUDA tensor [nvec]) and out (float64 CUDA tensor
+        [E, 4, nq^3], overwritten: rho, m_x, m_y, m_z).  Asynchronous."""
+        import torch
+        px, ldx = self._block(X)
+        nvec = ldx if nvec is None else nvec
+        n = self.ncells * 4 * self.nq ** 3
+        for t, size in ((occ, nvec), (out, n)):
+            if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() < size:
+                raise ValueError("occ / out must be contiguous float64 CUDA tensors of the stated size")
+        self._chk(self.lib.gbc_density_dev(self.h, px, ct.c_void_p(occ.data_ptr()),
+                                           ct.c_void_p(out.data_ptr()), int(nvec), int(ldx),
+                                           _stream_ptr(stream)))
 
     def set_delta(self, delta):
         d = np.ascontiguousarray(delta, dtype=np.complex128)
