@@ -40,6 +40,29 @@ template <typename T, int NP, int NQ> struct InterpTab {
   double jac;
 };
 
+// Per-thread running sum over the vectors.  FP64 blocks add in FP64.  FP32 blocks
+// add in FP32 with Kahan compensation (error ~2 ulp of the sum for any vector
+// count) and convert once at the end: GB300's FP64 pipe is a small fraction of
+// its FP32 rate, and a per-product FP64 add would dominate the kernel.
+template <typename T> struct QAcc;
+template <> struct QAcc<double> {
+  double s;
+  __device__ __forceinline__ void zero() { s = 0.0; }
+  __device__ __forceinline__ void add(double w, double x) { s = fma(w, x, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct QAcc<float> {
+  float s, c;   // sum, and the low-order part lost by the last additions (negated)
+  __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+  __device__ __forceinline__ void add(float w, float x) {   // s += w x, compensated
+    const float y = __fmaf_rn(w, x, -c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <int NQ> __device__ __forceinline__ int gidx(int x, int y, int z) {
   return x + y * (NQ + 1) + z * (NQ + 1) * (NQ + 1);
 }
@@ -116,13 +139,17 @@ __device__ __forceinline__ void interp_to_pencils(cplx<T>* P1, cplx<T>* P2, int 
   __syncthreads();
 }
 
-template <typename T, int NP, int NQ, int VB>
+template <typename T, int NP, int NQ, int VB, bool SAME>
 __global__ void __launch_bounds__(VB * 64)
 quad_grad_kernel(const GradArgs<T> a, const InterpTab<T, NP, NQ> tb) {
   using C = cplx<T>;
   constexpr int TPV = 64;
   constexpr int BUF = (NQ + 1) * (NQ + 1) * NQ;
   constexpr int VSTRIDE = 2 * BUF * 2 + 1;
+  constexpr int NLOAD = (NP * NP * NP + TPV - 1) / TPV;   // cell nodes staged per lane
+  // FP32: node rows computed once per CTA (fits the register budget of 3 CTAs per SM);
+  // FP64 recomputes them per vector step (its accumulators leave no room)
+  constexpr bool HOIST = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int v = threadIdx.x % VB;
@@ -132,37 +159,54 @@ quad_grad_kernel(const GradArgs<T> a, const InterpTab<T, NP, NQ> tb) {
   const int cx = e % nx, cy = (e / nx) % ny, cz = e / (nx * ny);
   C* P1 = buf + v * VSTRIDE;
   C* P2 = P1 + BUF * 2;
-  double acc[4][NQ];
+  // global row 2 I (< 2^31, checked by the launcher) and staging slot of the cell
+  // nodes this lane loads (-1: none)
+  auto node_of = [&](int k, int& row, int& slot) {
+    const int i = lane + k * TPV;
+    row = -1;
+    slot = -1;
+    if (i < NP * NP * NP) {
+      const int ix = i % NP, iy = (i / NP) % NP, iz = i / (NP * NP);
+      const long long I = gbc_node(a.mesh, cx, cy, cz, ix, iy, iz);
+      row = I >= 0 ? (int)(2 * I) : -1;
+      slot = gidx<NQ>(ix, iy, iz);
+    }
+  };
+  int rows[HOIST ? NLOAD : 1], slots[HOIST ? NLOAD : 1];
+  if constexpr (HOIST) {
+#pragma unroll
+    for (int k = 0; k < NLOAD; ++k) node_of(k, rows[k], slots[k]);
+  }
+  QAcc<T> acc[4][NQ];
 #pragma unroll
   for (int c = 0; c < 4; ++c)
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[c][q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[c][q].zero();
 
   for (int v0 = 0; v0 < a.nvec; v0 += VB) {
     const int vec = v0 + v;
     const bool vok = vec < a.nvec;
     C ua[2][NQ], ub[2][NQ];
 #pragma unroll
-    for (int which = 0; which < 2; ++which) {
-      if (which == 1 && a.A == a.B) {   // a^H S a: one interpolation serves both sides
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-          for (int q = 0; q < NQ; ++q) ub[s][q] = ua[s][q];
-        continue;
-      }
+    for (int which = 0; which < (SAME ? 1 : 2); ++which) {
       const cplx<T>* src = which == 0 ? a.A : a.B;
-      for (int i = lane; i < NP * NP * NP; i += TPV) {
-        const int ix = i % NP, iy = (i / NP) % NP, iz = i / (NP * NP);
-        const long long I = gbc_node(a.mesh, cx, cy, cz, ix, iy, iz);
-        C u = cmake<C>(0, 0), d = cmake<C>(0, 0);
-        if (I >= 0 && vok) {
-          u = src[(I * 2 + 0) * a.ldx + vec];
-          d = src[(I * 2 + 1) * a.ldx + vec];
+#pragma unroll(HOIST ? NLOAD : 1)
+      for (int k = 0; k < NLOAD; ++k) {
+        int row, slot;
+        if constexpr (HOIST) {
+          row = rows[k];
+          slot = slots[k];
+        } else {
+          node_of(k, row, slot);
         }
-        const int q = gidx<NQ>(ix, iy, iz);
-        P1[2 * q] = u;
-        P1[2 * q + 1] = d;
+        if (slot < 0) continue;
+        C u = cmake<C>(0, 0), d = cmake<C>(0, 0);
+        if (row >= 0 && vok) {
+          u = src[(long long)row * a.ldx + vec];
+          d = src[((long long)row + 1) * a.ldx + vec];
+        }
+        P1[2 * slot] = u;
+        P1[2 * slot + 1] = d;
       }
       __syncthreads();
       if (which == 0)
@@ -171,18 +215,30 @@ quad_grad_kernel(const GradArgs<T> a, const InterpTab<T, NP, NQ> tb) {
         interp_to_pencils<T, NP, NQ, TPV>(P1, P2, lane, tb, ub);
     }
     if (lane < NQ * NQ && vok) {
-      const double w = a.wv ? a.wv[vec] : 1.0;
+      const T w = (T)(a.wv ? a.wv[vec] : 1.0);
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
-        const C au = ua[0][q], ad = ua[1][q], bu = ub[0][q], bd = ub[1][q];
-        // Re(a^H b), Re(a^H sx b), Re(a^H sy b), Re(a^H sz b)
-        const T uu = au.x * bu.x + au.y * bu.y, dd = ad.x * bd.x + ad.y * bd.y;
-        const T ud_re = au.x * bd.x + au.y * bd.y, du_re = ad.x * bu.x + ad.y * bu.y;
-        const T ud_im = au.x * bd.y - au.y * bd.x, du_im = ad.x * bu.y - ad.y * bu.x;
-        acc[0][q] += w * (double)(uu + dd);
-        acc[1][q] += w * (double)(ud_re + du_re);
-        acc[2][q] += w * (double)(ud_im - du_im);
-        acc[3][q] += w * (double)(uu - dd);
+        const C au = ua[0][q], ad = ua[1][q];
+        if (SAME) {
+          // |u|^2, |d|^2 and u* d: (rho, m) = (uu + dd, 2 Re, 2 Im, uu - dd)
+          const T uu = au.x * au.x + au.y * au.y, dd = ad.x * ad.x + ad.y * ad.y;
+          const T re = au.x * ad.x + au.y * ad.y, im = au.x * ad.y - au.y * ad.x;
+          const T w2 = w + w;
+          acc[0][q].add(w, uu + dd);
+          acc[1][q].add(w2, re);
+          acc[2][q].add(w2, im);
+          acc[3][q].add(w, uu - dd);
+        } else {
+          const C bu = ub[0][q], bd = ub[1][q];
+          // Re(a^H b), Re(a^H sx b), Re(a^H sy b), Re(a^H sz b)
+          const T uu = au.x * bu.x + au.y * bu.y, dd = ad.x * bd.x + ad.y * bd.y;
+          const T ud_re = au.x * bd.x + au.y * bd.y, du_re = ad.x * bu.x + ad.y * bu.y;
+          const T ud_im = au.x * bd.y - au.y * bd.x, du_im = ad.x * bu.y - ad.y * bu.x;
+          acc[0][q].add(w, uu + dd);
+          acc[1][q].add(w, ud_re + du_re);
+          acc[2][q].add(w, ud_im - du_im);
+          acc[3][q].add(w, uu - dd);
+        }
       }
     }
   }
@@ -193,7 +249,7 @@ quad_grad_kernel(const GradArgs<T> a, const InterpTab<T, NP, NQ> tb) {
 #pragma unroll
     for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) red[((v * 64 + lane) * 4 + c) * NQ + q] = acc[c][q];
+      for (int q = 0; q < NQ; ++q) red[((v * 64 + lane) * 4 + c) * NQ + q] = acc[c][q].value();
   }
   __syncthreads();
   if (v == 0 && lane < NQ * NQ) {
@@ -234,10 +290,11 @@ cudaError_t launch_quad_grad_p(const gbc_ctx* c, const cplx<T>* A, const cplx<T>
   for (int q = 0; q < NQ; ++q) tb.wq[q] = c->tab.gq_w[q];
   tb.jac = c->h[0] * c->h[1] * c->h[2] / 8.0;
   constexpr size_t smem = quad_grad_smem<T, NP, NQ, VB>();
-  auto k = quad_grad_kernel<T, NP, NQ, VB>;
+  auto k = A == B ? quad_grad_kernel<T, NP, NQ, VB, true> : quad_grad_kernel<T, NP, NQ, VB, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (c->mesh.E <= 0 || nvec <= 0) return cudaSuccess;
+  if (2 * (long long)c->mesh.M >= (1LL << 31)) return cudaErrorInvalidValue;   // 32-bit rows
   k<<<c->mesh.E, VB * 64, smem, s>>>(a, tb);
   return cudaGetLastError();
 }
