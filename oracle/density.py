@@ -10,6 +10,10 @@ every cell (the points at which the paper's Eqs. disvxc / disbxc want V_xc and B
 Written out component by component:
     rho = |u|^2 + |d|^2,  m_x = 2 Re(u* d),  m_y = 2 Im(u* d),  m_z = |u|^2 - |d|^2
 for psi = (u, d) (spin up, spin down).
+
+Occupations (Sec. II: f_nk with the electron count fixed by the Lagrange multiplier mu;
+Sec. V: Fermi-Dirac smearing): f_nk = 1 / (1 + exp((eps_nk - mu) / kT)), one electron per
+spinor state, mu the root of sum_k w_k sum_n f_nk = N_e (w_k the Brillouin-zone weights).
 """
 from __future__ import annotations
 
@@ -41,3 +45,34 @@ def densities(d, X, occ, cells=None):
     rho = (uu + dd) @ occ
     m = np.stack([(2.0 * ud.real) @ occ, (2.0 * ud.imag) @ occ, (uu - dd) @ occ])
     return rho, m
+
+
+def fermi(x):
+    """1 / (1 + e^x), evaluated without overflow."""
+    x = np.asarray(x, np.float64)
+    out = np.empty_like(x)
+    pos = x > 0
+    ep = np.exp(-x[pos])
+    out[pos] = ep / (1.0 + ep)
+    out[~pos] = 1.0 / (1.0 + np.exp(x[~pos]))
+    return out
+
+
+def fermi_occupations(eps, kweights, nelec, kT):
+    """f[k, n] and mu with sum_k w_k sum_n f[k, n] = nelec (root by Brent's method)."""
+    from scipy.optimize import brentq
+    eps = np.atleast_2d(np.asarray(eps, np.float64))
+    w = np.asarray(kweights, np.float64)
+
+    def excess(mu):
+        return float((w[:, None] * fermi((eps - mu) / kT)).sum()) - nelec
+
+    lo, hi = eps.min() - 60.0 * kT, eps.max() + 60.0 * kT
+    for _ in range(100):                     # N(mu) increases with mu: widen the bracket
+        if excess(lo) <= 0 <= excess(hi):
+            break
+        lo, hi = lo - 60.0 * kT, hi + 60.0 * kT
+    else:
+        raise ValueError("no chemical potential brackets the electron count")
+    mu = brentq(excess, lo, hi, xtol=1e-15, rtol=1e-15, maxiter=500)
+    return fermi((eps - mu) / kT), mu

@@ -120,3 +120,41 @@ def test_su2_rotation_covariance(disc):
     np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-14)
     np.testing.assert_allclose(rho2, rho, rtol=1e-12, atol=1e-13)
     np.testing.assert_allclose(m2, np.einsum("ij,jeq->ieq", R, m), rtol=1e-11, atol=1e-12)
+
+
+# ---- Fermi-Dirac occupations (Sec. II electron-count constraint, Sec. V smearing) -------
+KT = 500.0 * 3.166811563e-6          # 500 K in Ha
+
+
+def test_fermi_count_and_bounds():
+    rng = np.random.default_rng(3)
+    eps = np.sort(rng.uniform(-1.0, 2.0, (3, 40)), axis=1)
+    w = np.array([0.25, 0.5, 0.25])
+    f, mu = od.fermi_occupations(eps, w, 17.3, KT)
+    assert abs((w[:, None] * f).sum() - 17.3) < 1e-11
+    assert np.all((f >= 0) & (f <= 1))
+    # decreasing in eps within every k-point, and 1/2 at eps = mu
+    assert np.all(np.diff(f, axis=1) <= 0)
+    np.testing.assert_allclose(od.fermi(np.zeros(1)), [0.5])
+
+
+def test_fermi_closed_forms():
+    # one state holding a fraction q: mu = eps + kT ln(q / (1 - q))
+    for q in (0.1, 0.5, 0.93):
+        f, mu = od.fermi_occupations([[0.3]], [1.0], q, KT)
+        np.testing.assert_allclose(mu, 0.3 + KT * np.log(q / (1 - q)), rtol=0, atol=1e-14)
+        np.testing.assert_allclose(f[0, 0], q, rtol=1e-12)
+    # a spectrum symmetric about c at half filling: mu = c (f(-x) = 1 - f(x))
+    half = np.random.default_rng(4).uniform(0.001, 0.01, 12)
+    eps = np.concatenate([0.2 - half, 0.2 + half])[None, :]
+    f, mu = od.fermi_occupations(eps, [1.0], 12.0, KT)
+    assert abs(mu - 0.2) < 1e-13
+
+
+def test_fermi_aufbau_limit():
+    # a gap much larger than kT: the N_e lowest states (over all k-points) are full
+    eps = np.array([[-0.5, -0.2, 0.4, 0.9], [-0.45, 0.5, 0.6, 1.0]])
+    f, mu = od.fermi_occupations(eps, [0.5, 0.5], 1.5, KT)
+    full = np.array([[1, 1, 0, 0], [1, 0, 0, 0]], float)
+    np.testing.assert_allclose(f, full, atol=1e-12)
+    assert -0.2 < mu < 0.4
