@@ -237,6 +237,18 @@ gbc_status gbc_set_delta(gbc_ctx* ctx, const double* delta);
  * Synchronous; uses library workspace. */
 gbc_status gbc_density_dev(gbc_ctx* ctx, const void* X, const double* occ, double* out, int nvec,
                            int ldx, void* stream);
+
+/* Fermi-Dirac occupations of Ritz values (Sec. II: f_nk with the electron count
+ * fixed by the Lagrange multiplier mu; Sec. V: Fermi-Dirac smearing):
+ * f_nk = 1 / (1 + exp((eps_nk - mu) / kT)), one electron per spinor state, mu the
+ * root of sum_k w_k sum_n f_nk = nelec.  eps: host [nk][nstates] (Ha); kweights:
+ * host nk non-negative Brillouin-zone weights (NULL: 1/nk each); kT in Ha (500 K
+ * = 1.583e-3 Ha); occ: host [nk][nstates], written; *mu_out (may be NULL).
+ * Host computation, no device or context needed; bisection to adjacent doubles.
+ * GBC_EINVAL for a null eps/occ, nk or nstates < 1, kT <= 0, non-finite input,
+ * a negative weight, or nelec outside (0, nstates * sum_k w_k). */
+gbc_status gbc_fermi_occupations(const double* eps, const double* kweights, int nk, int nstates,
+                                 double nelec, double kT, double* occ, double* mu_out);
 gbc_status gbc_density(gbc_ctx* ctx, const void* X, const double* occ, double* rho, double* mag,
                        int nvec, int ldx, void* stream);
 

@@ -31,7 +31,7 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_batch_last_error", "gbc_batch_filter", "gbc_batch_launches", "gbc_tune",
            "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta",
            "gbc_tc_gemm_nt", "gbc_tc_wait_selftest", "gbc_set_nonlocal_engine", "gbc_get_nonlocal_engine",
-           "gbc_sync_status", "gbc_density", "gbc_density_dev"]
+           "gbc_sync_status", "gbc_density", "gbc_density_dev", "gbc_fermi_occupations"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "gbc_set_delta": ([P, DP], I),
         "gbc_density": ([P, V, DP, DP, DP, I, I, V], I),
         "gbc_density_dev": ([P, V, V, V, I, I, V], I),
+        "gbc_fermi_occupations": ([DP, DP, I, I, D, D, DP, DP], I),
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
         "gbc_tc_wait_selftest": ([I, V], I),
         "gbc_set_nonlocal_engine": ([P, I], I),
@@ -109,6 +110,23 @@ def _iarr(a):
 def _darr(a):
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a, a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def fermi_occupations(eps, kweights, nelec, kT):
+    """Fermi-Dirac occupations of Ritz values eps [nk, nstates] (Ha) with Brillouin-zone
+    weights (None: equal) and mu fixed by the electron count; returns (occ, mu)."""
+    lib = load_library()
+    e, ep = _darr(np.atleast_2d(np.asarray(eps, np.float64)))
+    nk, ns = e.shape
+    w, wp = (None, None) if kweights is None else _darr(np.asarray(kweights, np.float64))
+    occ = np.zeros_like(e)
+    mu = ct.c_double()
+    st = lib.gbc_fermi_occupations(ep, wp, int(nk), int(ns), float(nelec), float(kT),
+                                   occ.ctypes.data_as(ct.POINTER(ct.c_double)), ct.byref(mu))
+    if st != 0:
+        raise GbcError(st, "gbc_fermi_occupations: invalid arguments" if st == 1 else
+                       "gbc_fermi_occupations: no bracket for the chemical potential")
+    return occ, mu.value
 
 
 def _stream_ptr(stream):
