@@ -230,13 +230,15 @@ gbc_status gbc_set_delta(gbc_ctx* ctx, const double* delta);
  *
  * gbc_density_dev: occ and out are DEVICE arrays; out [E][4][nq^3] doubles
  * (cell-major; component 0 rho, 1..3 m_x, m_y, m_z; Gauss point q = (qz nq + qy)
- * nq + qx) is overwritten.  Asynchronous on ``stream``; one kernel launch, and no
- * allocation once the operator tables are built (see gbc_apply_h_noalloc).
+ * nq + qx) is overwritten (accumulate = 0) or added to (accumulate != 0: sums over
+ * k-points, with the Brillouin-zone weight folded into occ).  Asynchronous on
+ * ``stream``; one kernel launch, and no allocation once the operator tables are
+ * built (see gbc_apply_h_noalloc).
  * gbc_density: occ, rho and mag are HOST arrays; rho [E][nq^3] and mag
  * [3][E][nq^3] (layout as gbc_set_fields; mag may be NULL) are written.
  * Synchronous; uses library workspace. */
 gbc_status gbc_density_dev(gbc_ctx* ctx, const void* X, const double* occ, double* out, int nvec,
-                           int ldx, void* stream);
+                           int ldx, int accumulate, void* stream);
 
 /* Fermi-Dirac occupations of Ritz values (Sec. II: f_nk with the electron count
  * fixed by the Lagrange multiplier mu; Sec. V: Fermi-Dirac smearing):

@@ -326,8 +326,8 @@ gbc_status energy_grad_t(gbc_ctx* c, const cplx<T>* Y, const double* w, cplx<T>*
 // rho and m at the Gauss points (Eqs. rho, mag) into out [E][4][nq^3] (device)
 template <typename T>
 cudaError_t density_t(const gbc_ctx* c, const cplx<T>* X, const double* occ_dev, double* out,
-                      int nvec, int ldx, cudaStream_t s) {
-  return quad_grad<T>(c, X, X, occ_dev, 1.0, nvec, ldx, out, s, 1);
+                      int nvec, int ldx, int accumulate, cudaStream_t s) {
+  return quad_grad<T>(c, X, X, occ_dev, 1.0, nvec, ldx, out, s, accumulate ? 2 : 1);
 }
 
 gbc_status density_check(gbc_ctx* c, const void* X, const double* occ, const double* out, int nvec,
@@ -344,14 +344,14 @@ gbc_status density_check(gbc_ctx* c, const void* X, const double* occ, const dou
 extern "C" {
 
 gbc_status gbc_density_dev(gbc_ctx* c, const void* X, const double* occ, double* out, int nvec,
-                           int ldx, void* stream) {
+                           int ldx, int accumulate, void* stream) {
   if (!c) return GBC_EINVAL;
   GBC_TRY(density_check(c, X, occ, out, nvec, ldx));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->prec == GBC_FP64)
-    GBC_CU(c, density_t<double>(c, (const double2*)X, occ, out, nvec, ldx, s));
+    GBC_CU(c, density_t<double>(c, (const double2*)X, occ, out, nvec, ldx, accumulate, s));
   else
-    GBC_CU(c, density_t<float>(c, (const float2*)X, occ, out, nvec, ldx, s));
+    GBC_CU(c, density_t<float>(c, (const float2*)X, occ, out, nvec, ldx, accumulate, s));
   return GBC_OK;
 }
 
@@ -364,9 +364,9 @@ gbc_status gbc_density(gbc_ctx* c, const void* X, const double* occ, double* rho
   GBC_TRY(grad_scratch(c, nvec, &gs));
   GBC_CU(c, cudaMemcpyAsync(gs.wv, occ, sizeof(double) * nvec, cudaMemcpyHostToDevice, s));
   if (c->prec == GBC_FP64)
-    GBC_CU(c, density_t<double>(c, (const double2*)X, gs.wv, gs.g, nvec, ldx, s));
+    GBC_CU(c, density_t<double>(c, (const double2*)X, gs.wv, gs.g, nvec, ldx, 0, s));
   else
-    GBC_CU(c, density_t<float>(c, (const float2*)X, gs.wv, gs.g, nvec, ldx, s));
+    GBC_CU(c, density_t<float>(c, (const float2*)X, gs.wv, gs.g, nvec, ldx, 0, s));
   return download_quad(c, gs.g, rho, mag, s);
 }
 

@@ -9,7 +9,7 @@
 // contractions of Eqs. rho and mag with the adjoint as the bra.
 //
 // Point-wise mode (A = B, wv = occupations): g[e][c][q] = scale * sum_v wv[v]
-// Re(a_v^H S_c a_v), written rather than accumulated and without w_q J, is
+// Re(a_v^H S_c a_v), without w_q J, written (mode 1) or added (mode 2), is
 // (rho, m_x, m_y, m_z) at the Gauss points (Eqs. rho, mag).
 //
 // One CTA owns one cell and walks all vectors in chunks of VB, so every g[e]
@@ -31,7 +31,7 @@ template <typename T> struct GradArgs {
   int ldx, nvec;
   double scale;
   MeshDev mesh;
-  int pointwise;       // 1: g = scale * sum (no w_q J, overwrite)
+  int pointwise;       // 1: g = scale * sum, 2: g += scale * sum (no w_q J either way)
 };
 
 template <typename T, int NP, int NQ> struct InterpTab {
@@ -262,8 +262,10 @@ quad_grad_kernel(const GradArgs<T> a, const InterpTab<T, NP, NQ> tb) {
         for (int w = 0; w < VB; ++w) sum += red[((w * 64 + lane) * 4 + c) * NQ + qz];
         const int q = (qz * NQ + y) * NQ + x;
         double* dst = &a.g[((size_t)e * 4 + c) * NQ * NQ * NQ + q];
-        if (a.pointwise) {
+        if (a.pointwise == 1) {
           *dst = a.scale * sum;
+        } else if (a.pointwise == 2) {
+          *dst += a.scale * sum;
         } else {
           const double wq = tb.wq[x] * tb.wq[y] * tb.wq[qz] * tb.jac;
           *dst += a.scale * wq * sum;

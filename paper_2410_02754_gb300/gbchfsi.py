@@ -85,7 +85,7 @@ def load_library(path: str = LIB_PATH):
         "gbc_energy_grad": ([P, V, DP, V, DP, DP, DP, DP, I, I, V], I),
         "gbc_set_delta": ([P, DP], I),
         "gbc_density": ([P, V, DP, DP, DP, I, I, V], I),
-        "gbc_density_dev": ([P, V, V, V, I, I, V], I),
+        "gbc_density_dev": ([P, V, V, V, I, I, I, V], I),
         "gbc_fermi_occupations": ([DP, DP, I, I, D, D, DP, DP], I),
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
         "gbc_tc_wait_selftest": ([I, V], I),
@@ -373,9 +373,10 @@ class Context:
                                        _stream_ptr(stream)))
         return rho.reshape(self.ncells, -1), mag.reshape(3, self.ncells, -1)
 
-    def density_dev(self, X, occ, out, nvec=None, stream=None):
+    def density_dev(self, X, occ, out, nvec=None, accumulate=False, stream=None):
         """Device form: occ (float64 CUDA tensor [nvec]) and out (float64 CUDA tensor
-        [E, 4, nq^3], overwritten: rho, m_x, m_y, m_z).  Asynchronous."""
+        [E, 4, nq^3]: rho, m_x, m_y, m_z; overwritten, or added to with accumulate).
+        Asynchronous."""
         import torch
         px, ldx = self._block(X)
         nvec = ldx if nvec is None else nvec
@@ -385,7 +386,7 @@ class Context:
                 raise ValueError("occ / out must be contiguous float64 CUDA tensors of the stated size")
         self._chk(self.lib.gbc_density_dev(self.h, px, ct.c_void_p(occ.data_ptr()),
                                            ct.c_void_p(out.data_ptr()), int(nvec), int(ldx),
-                                           _stream_ptr(stream)))
+                                           int(bool(accumulate)), _stream_ptr(stream)))
 
     def set_delta(self, delta):
         d = np.ascontiguousarray(delta, dtype=np.complex128)
