@@ -19,11 +19,14 @@ What it computes (each function cites the passage it follows):
 * ``grad``    -- reverse-mode gradients of L = sum_i w_i y_i^H H y_i through
                  the filter.
 * ``density`` -- electron density rho and magnetisation density m at the Gauss
-                 points from an occupied spinor block (Eqs. rho, mag).
+                 points from an occupied spinor block (Eqs. rho, mag), and
+                 Fermi-Dirac occupations with the electron-count chemical potential.
+* ``twogrid`` -- transfer of a block from FE order p_c to p_f >= p_c on the same
+                 mesh by nodal interpolation (Eq. FEWfnsCMesh, two-grid strategy).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests in
-``tests/test_oracle_pins.py``, ``tests/test_oracle_grad.py`` and
-``tests/test_oracle_density.py`` except the residual-split reformulation's
+``tests/test_oracle_pins.py``, ``tests/test_oracle_grad.py``,
+``tests/test_oracle_density.py`` and ``tests/test_oracle_twogrid.py`` except the residual-split reformulation's
 relation to the authors' unpublished variant ("parity unpinned" for that
 relation only; its exact equality with the direct filter is pinned).
 """
