@@ -169,6 +169,15 @@ def flops_per_cell_vector(p: int, nq: int, kpt: bool) -> int:
     return kin + interp + test + pointwise
 
 
+def hbm_peak():
+    """Measured copy bandwidth of this machine's GPUs (GB/s) and where it came from."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback (6.8 TB/s)"
+
+
 def build_contexts(g, prob, ks, prec, nl_engine=1):
     import torch
     ctxs = []
@@ -360,6 +369,43 @@ def run_gpu(args):
                        "warm-up, CUDA events; bytes = X read once + rho/m written (FP64)"}
         except Exception as exc:   # an auxiliary leg must not cost the headline line
             out["density"] = {"error": f"{type(exc).__name__}: {exc}"}
+
+    # ---- two-grid transfer (Eq. FEWfnsCMesh): the order-5 block of the same mesh carried to
+    # order 6 (the bench mesh), 256 vectors FP32, device-resident, CUDA events
+    if not args.no_twogrid and rank == 0 and prob.p > 2:
+        try:
+            pc = prob.p - 1
+            cc = g.Context(torch.cuda.current_device())
+            cc.set_mesh(prob.ncell, prob.h, pc, pc + 2, prob.periodic)
+            cc.set_precision(g.FP32)
+            xc = torch.randn((cc.nnodes, 2, nvec), dtype=torch.complex64, device="cuda")
+            xf = torch.empty_like(X32[0])
+            c = ctx32[0]
+            for _ in range(3):
+                c.prolongate_from(cc, xc, xf)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nrep = 5
+            e0.record(stream)
+            for _ in range(nrep):
+                c.prolongate_from(cc, xc, xf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_t = e0.elapsed_time(e1) / nrep
+            by = (xc.numel() + xf.numel()) * xf.element_size()
+            peak, peak_src = hbm_peak()
+            gbs = by / (ms_t / 1e3) / 1e9
+            out["twogrid"] = {
+                "ms": round(ms_t, 4), "kernel": f"k_prolongate<float,{pc + 1},{prob.p + 1},16>",
+                "algorithmic_bytes": by, "achieved_gbs": round(gbs, 1),
+                "frac_hbm": round(gbs / peak, 4), "peak_gbs": peak, "peak_note": peak_src,
+                "how": f"order {pc} -> {prob.p} on the bench mesh, {nvec} vectors FP32, {nrep} "
+                       "launches after 3 warm-up; bytes = coarse block read once + fine block "
+                       "written once"}
+            cc.close()
+            del xc, xf
+        except Exception as exc:   # an auxiliary leg must not cost the headline line
+            out["twogrid"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     # ---- FP64 filter and accuracy of the mixed path at the same inputs (k-point 0):
     # three chains from the same seeded block -- FP64, mixed direct, mixed residual-split --
@@ -652,6 +698,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-density", action="store_true")
+    ap.add_argument("--no-twogrid", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--cycles", type=int, default=3, help="ChFSI cycles of the accuracy leg")

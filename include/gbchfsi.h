@@ -254,6 +254,22 @@ gbc_status gbc_fermi_occupations(const double* eps, const double* kweights, int 
 gbc_status gbc_density(gbc_ctx* ctx, const void* X, const double* occ, double* rho, double* mag,
                        int nvec, int ldx, void* stream);
 
+/* ---- two-grid strategy (Sec. IV.A, Eq. FEWfnsCMesh) ---------------------------- */
+
+/* Carry a block from the order-p_c discretisation of ``coarse`` to the order-p_f
+ * discretisation of ``fine`` on the same mesh (same ncell, h and periodic flags;
+ * p_f = p_c or p_c + 1; same precision and device): the order-p_c space lies in
+ * the order-p_f space, so the coarse FE function is reproduced exactly by nodal
+ * interpolation, Xf[J] = sum_I N^{p_c}_I(r_J) Xc[I] at every free fine node r_J.
+ * Xc: device block [M_c][2][ldxc]; Xf: device block [M_f][2][ldxf], columns
+ * 0..nvec-1 written, distinct from Xc.  Only the meshes of the two contexts are
+ * used (no fields or projectors needed).  Asynchronous on ``stream``; errors are
+ * reported on ``fine``: GBC_EINVAL for null or equal blocks, nvec < 1, ldx < nvec,
+ * different devices, precisions or meshes; GBC_ESTATE if a mesh is not set;
+ * GBC_EUNSUPPORTED for another order pair. */
+gbc_status gbc_prolongate(gbc_ctx* coarse, gbc_ctx* fine, const void* Xc, int ldxc, void* Xf,
+                          int ldxf, int nvec, void* stream);
+
 /* ---- batched systems (independent k-points / systems, Sec. III.B) ------------ */
 
 typedef struct gbc_batch gbc_batch;   /* opaque, owned by the library */

@@ -26,8 +26,9 @@ def transfer_matrix_1d(pc: int, pf: int) -> np.ndarray:
     return np.asarray(L).T
 
 
-def prolongate(dc, df, Xc):
-    """X_f [M_f][2][nv] from X_c [M_c][2][nv]; dc, df are Discretisations of the same cells."""
+def prolongate(dc, df, Xc, cells=None):
+    """X_f [M_f][2][nv] from X_c [M_c][2][nv]; dc, df are Discretisations of the same cells.
+    With ``cells``, only the fine nodes of those cells are filled (the rest stay zero)."""
     mc, mf = dc.mesh, df.mesh
     if mc.ncell != mf.ncell or mc.periodic != mf.periodic or not np.allclose(mc.h, mf.h):
         raise ValueError("coarse and fine discretisations must share the mesh")
@@ -36,11 +37,12 @@ def prolongate(dc, df, Xc):
     # 3-D weights W[(jz, jy, jx), (iz, iy, ix)] = T[jx, ix] T[jy, iy] T[jz, iz]
     W = np.einsum("ad,be,cf->cbafed", T, T, T).reshape(nf ** 3, nc ** 3)
     nv = Xc.shape[2]
-    Xp = np.concatenate([np.asarray(Xc, np.complex128), np.zeros((1, 2, nv), np.complex128)])
     Xf = np.zeros((mf.nnodes, 2, nv), np.complex128)
-    for e in range(mc.ncells):
+    for e in (range(mc.ncells) if cells is None else cells):
         ic = mc.cell_nodes[e]
-        vals = W @ Xp[np.where(ic >= 0, ic, mc.nnodes)].reshape(nc ** 3, -1)
+        xe = np.asarray(Xc)[np.maximum(ic, 0)].astype(np.complex128)
+        xe[ic < 0] = 0.0
+        vals = W @ xe.reshape(nc ** 3, -1)
         jf = mf.cell_nodes[e]
         ok = jf >= 0
         Xf[jf[ok]] = vals.reshape(nf ** 3, 2, nv)[ok]

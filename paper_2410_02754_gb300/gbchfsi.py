@@ -31,7 +31,8 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_batch_last_error", "gbc_batch_filter", "gbc_batch_launches", "gbc_tune",
            "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta",
            "gbc_tc_gemm_nt", "gbc_tc_wait_selftest", "gbc_set_nonlocal_engine", "gbc_get_nonlocal_engine",
-           "gbc_sync_status", "gbc_density", "gbc_density_dev", "gbc_fermi_occupations"]
+           "gbc_sync_status", "gbc_density", "gbc_density_dev", "gbc_fermi_occupations",
+           "gbc_prolongate"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -87,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "gbc_density": ([P, V, DP, DP, DP, I, I, V], I),
         "gbc_density_dev": ([P, V, V, V, I, I, I, V], I),
         "gbc_fermi_occupations": ([DP, DP, I, I, D, D, DP, DP], I),
+        "gbc_prolongate": ([P, P, V, I, V, I, I, V], I),
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
         "gbc_tc_wait_selftest": ([I, V], I),
         "gbc_set_nonlocal_engine": ([P, I], I),
@@ -387,6 +389,15 @@ class Context:
         self._chk(self.lib.gbc_density_dev(self.h, px, ct.c_void_p(occ.data_ptr()),
                                            ct.c_void_p(out.data_ptr()), int(nvec), int(ldx),
                                            int(bool(accumulate)), _stream_ptr(stream)))
+
+    def prolongate_from(self, coarse, Xc, Xf, nvec=None, stream=None):
+        """Two-grid transfer into this (fine, order p or p_c + 1) context's block Xf from
+        the block Xc of ``coarse`` (order p_c, same mesh): exact nodal interpolation."""
+        pc, ldxc = coarse._block(Xc)
+        pf, ldxf = self._block(Xf)
+        nvec = min(ldxc, ldxf) if nvec is None else nvec
+        self._chk(self.lib.gbc_prolongate(coarse.h, self.h, pc, int(ldxc), pf, int(ldxf),
+                                          int(nvec), _stream_ptr(stream)))
 
     def set_delta(self, delta):
         d = np.ascontiguousarray(delta, dtype=np.complex128)
