@@ -23,10 +23,14 @@ What it computes (each function cites the passage it follows):
                  Fermi-Dirac occupations with the electron-count chemical potential.
 * ``twogrid`` -- transfer of a block from FE order p_c to p_f >= p_c on the same
                  mesh by nodal interpolation (Eq. FEWfnsCMesh, two-grid strategy).
+* ``scf``     -- the SCF pieces around the eigensolver: an exchange-only local spin
+                 density stand-in for V_xc / B_xc (closed form), the density inner
+                 product (Eq. innerPdt) and Anderson mixing.
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py``, ``tests/test_oracle_grad.py``,
-``tests/test_oracle_density.py`` and ``tests/test_oracle_twogrid.py`` except the residual-split reformulation's
+``tests/test_oracle_density.py``, ``tests/test_oracle_twogrid.py`` and
+``tests/test_oracle_scf.py`` except the residual-split reformulation's
 relation to the authors' unpublished variant ("parity unpinned" for that
 relation only; its exact equality with the direct filter is pinned).
 """
