@@ -101,3 +101,20 @@ def test_anderson_finite_termination_on_linear_map():
         rs.append(r)
         x, _ = scf.anderson(W, xs, rs, 1.0)
     assert np.abs(x.reshape(-1) - xstar).max() < 1e-8
+
+
+def test_scf_loop_reaches_the_eigensolver_independent_fixed_point():
+    """The SCF loop with one ChFSI cycle per step and with exact eigenpairs converge to the
+    same self-consistent densities (the fixed point does not depend on the eigensolver)."""
+    z = np.zeros((8, 4 ** 3))
+    prob = syn.make_problem(ncell=(2, 2, 2), h=(1.0, 1.0, 1.0), p=2, natoms=2, rc=1.0, seed=9,
+                            well_depth=3.0, bmax=0.0).with_(bx=z, by=z, bz=z)
+    M = prob.nnodes
+    X0 = syn.random_block(M, 12, 3)               # 3 electrons, 9 buffer states
+    v0 = syn.random_start(M, 3)
+    args = dict(nelec=3.0, kT=0.05, degree=16, lanczos_steps=12, alpha=0.5, nhist=4, iters=30)
+    r_c, x_c, e_c = scf.scf_loop(prob, X0, v0, eig="chfsi", **args)
+    r_d, x_d, e_d = scf.scf_loop(prob, X0, v0, eig="dense", **args)
+    assert r_c[-1] < 1e-7 * r_c[0] and r_d[-1] < 1e-8 * r_d[0]
+    np.testing.assert_allclose(x_c, x_d, rtol=0, atol=1e-7 * np.abs(x_d).max())
+    np.testing.assert_allclose(e_c[:3], e_d[:3], rtol=0, atol=1e-8)
