@@ -254,6 +254,35 @@ gbc_status gbc_fermi_occupations(const double* eps, const double* kweights, int 
 gbc_status gbc_density(gbc_ctx* ctx, const void* X, const double* occ, double* rho, double* mag,
                        int nvec, int ldx, void* stream);
 
+/* ---- self-consistent field (Sec. III.B.1) ------------------------------------- */
+
+/* Fields of the next SCF step from the densities: V_eff = vext + V_xc(rho, m) and
+ * B_xc(rho, m) at every Gauss point, written into the context's fields (as
+ * gbc_set_fields would, without a host copy; the next hot-path call rebuilds the
+ * weighted tables).  V_xc, B_xc: a closed-form stand-in for the paper's PBE
+ * (Eqs. disvxc / disbxc for a functional without gradients) -- exchange-only local
+ * spin density of a noncollinear density: rho_up/dn = (rho +- |m|)/2 (clamped at 0),
+ * e = -(3/4) c (rho_up^(4/3) + rho_dn^(4/3)), c = (6/pi)^(1/3), V_xc = (v_up + v_dn)/2,
+ * B_xc = (v_up - v_dn)/2 m/|m| (0 where m = 0), v_s = -c rho_s^(1/3).
+ * dens: device [E][4][nq^3] doubles (rho, m_x, m_y, m_z: gbc_density_dev's layout);
+ * vext: device [E][nq^3] doubles; exc: device [E][nq^3] doubles receiving e, or NULL.
+ * Synchronous (returns after the kernel on ``stream``). */
+gbc_status gbc_scf_fields(gbc_ctx* ctx, const double* dens, const double* vext, double* exc,
+                          void* stream);
+
+/* Anderson mixing (Sec. III.B.1): from the last nhist (1..8) SCF inputs xin[j] and
+ * outputs xout[j] = F(xin[j]) (device [E][4][nq^3] arrays, oldest first; host arrays of
+ * device pointers), xnext = sum_j b_j ((1 - alpha) xin[j] + alpha xout[j]) with
+ * sum_j b_j = 1 and b minimising || sum_j b_j (xout[j] - xin[j]) || in the inner
+ * product of Eq. innerPdt, <(r1, m1), (r2, m2)> = (1/2)(int r1 r2 + int m1.m2) by the
+ * mesh's Gauss quadrature.  xnext may be one of xin.  coeffs: host nhist doubles (or
+ * NULL); resnorm: host, || xout[last] - xin[last] || (or NULL).  Synchronous.
+ * GBC_EINVAL for a bad count, alpha <= 0 or a null entry; GBC_ENOTPD if the residuals'
+ * Gram matrix is singular (repeated residuals). */
+gbc_status gbc_anderson_mix(gbc_ctx* ctx, const double* const* xin, const double* const* xout,
+                            int nhist, double alpha, double* xnext, double* coeffs,
+                            double* resnorm, void* stream);
+
 /* ---- two-grid strategy (Sec. IV.A, Eq. FEWfnsCMesh) ---------------------------- */
 
 /* Carry a block from the order-p_c discretisation of ``coarse`` to the order-p_f

@@ -32,7 +32,7 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta",
            "gbc_tc_gemm_nt", "gbc_tc_wait_selftest", "gbc_set_nonlocal_engine", "gbc_get_nonlocal_engine",
            "gbc_sync_status", "gbc_density", "gbc_density_dev", "gbc_fermi_occupations",
-           "gbc_prolongate"]
+           "gbc_prolongate", "gbc_scf_fields", "gbc_anderson_mix"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH):
         "gbc_density_dev": ([P, V, V, V, I, I, I, V], I),
         "gbc_fermi_occupations": ([DP, DP, I, I, D, D, DP, DP], I),
         "gbc_prolongate": ([P, P, V, I, V, I, I, V], I),
+        "gbc_scf_fields": ([P, V, V, V, V], I),
+        "gbc_anderson_mix": ([P, ct.POINTER(V), ct.POINTER(V), I, D, V, DP, DP, V], I),
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
         "gbc_tc_wait_selftest": ([I, V], I),
         "gbc_set_nonlocal_engine": ([P, I], I),
@@ -398,6 +400,37 @@ class Context:
         nvec = min(ldxc, ldxf) if nvec is None else nvec
         self._chk(self.lib.gbc_prolongate(coarse.h, self.h, pc, int(ldxc), pf, int(ldxf),
                                           int(nvec), _stream_ptr(stream)))
+
+    def _dens(self, t, comps):
+        import torch
+        n = self.ncells * comps * self.nq ** 3
+        if t is None:
+            return None
+        if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"expected a contiguous float64 CUDA tensor of {n} values")
+        return ct.c_void_p(t.data_ptr())
+
+    def scf_fields(self, dens, vext, exc=None, stream=None):
+        """V_eff = vext + V_xc and B_xc from dens [E, 4, nq^3] into this context's fields
+        (closed-form exchange-only local spin density stand-in).  Synchronous."""
+        self._chk(self.lib.gbc_scf_fields(self.h, self._dens(dens, 4), self._dens(vext, 1),
+                                          self._dens(exc, 1), _stream_ptr(stream)))
+
+    def anderson_mix(self, xin, xout, alpha, xnext, stream=None):
+        """Anderson mixing of the histories (lists of [E, 4, nq^3] tensors, oldest first)
+        into xnext; returns (coefficients, residual norm of the last pair)."""
+        n = len(xin)
+        if n != len(xout) or not 1 <= n <= 8:
+            raise ValueError("need 1..8 input/output pairs")
+        pin = (ct.c_void_p * n)(*[self._dens(x, 4) for x in xin])
+        pout = (ct.c_void_p * n)(*[self._dens(x, 4) for x in xout])
+        coef = np.zeros(n)
+        rn = ct.c_double()
+        self._chk(self.lib.gbc_anderson_mix(self.h, pin, pout, n, float(alpha),
+                                            self._dens(xnext, 4),
+                                            coef.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                            ct.byref(rn), _stream_ptr(stream)))
+        return coef, rn.value
 
     def set_delta(self, delta):
         d = np.ascontiguousarray(delta, dtype=np.complex128)
