@@ -432,7 +432,10 @@ def run_gpu(args):
         except Exception as exc:   # an auxiliary leg must not cost the headline line
             out["scf"] = {"error": f"{type(exc).__name__}: {exc}"}
         finally:                   # the accuracy leg below uses this context's original H
-            ctx32[0].set_fields(prob.veff, prob.bx, prob.by, prob.bz)
+            try:
+                ctx32[0].set_fields(prob.veff, prob.bx, prob.by, prob.bz)
+            except Exception as exc:
+                out.setdefault("scf", {})["restore_error"] = f"{type(exc).__name__}: {exc}"
 
     # ---- FP64 filter and accuracy of the mixed path at the same inputs (k-point 0):
     # three chains from the same seeded block -- FP64, mixed direct, mixed residual-split --
