@@ -279,9 +279,9 @@ def run_gpu(args):
     clocks = clk.summary()
     peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
     # DRAM bytes of one hx_local launch: ncu dram__bytes_read + write of the same kernel on the
-    # c1 mesh at 32 vectors (1.364 GB, of which 34 MB fields), scaled by the vector count
+    # cube16_p6 mesh at 32 vectors (1.364 GB, of which 34 MB fields), scaled by the vector count
     # (X gather and Y read-modify-write grow with it)
-    if args.config == "c1":
+    if args.config == "cube16_p6":
         traffic = 0.034e9 + (1.364e9 - 0.034e9) * nvec / 32
         traffic_note = "ncu capture at 32 vectors scaled by vectors; = algorithmic X read + Y RMW"
     else:
@@ -365,7 +365,7 @@ def run_gpu(args):
                 "algorithmic_bytes": by, "achieved_gbs": round(by / (ms_d / 1e3) / 1e9, 1),
                 "occupations": f"Fermi-Dirac, N_e = {nvec / 2:g}, 500 K, mu = {mu:.6f} Ha "
                                "(gbc_fermi_occupations on the k-point-0 Ritz values)",
-                "how": f"c1 k-point 0 filtered block ({nvec} vectors, FP32), {nrep} launches after 3 "
+                "how": f"cube16_p6 k-point 0 filtered block ({nvec} vectors, FP32), {nrep} launches after 3 "
                        "warm-up, CUDA events; bytes = X read once + rho/m written (FP64)"}
         except Exception as exc:   # an auxiliary leg must not cost the headline line
             out["density"] = {"error": f"{type(exc).__name__}: {exc}"}
@@ -504,7 +504,7 @@ def run_gpu(args):
 
 
 def run_batch(args):
-    """Config 2: sixteen uneven systems filtered by one batched call per step
+    """batch16: sixteen uneven systems filtered by one batched call per step
     (persistent cell-apply launches per FE order, CUDA-graph replay)."""
     import torch
 
@@ -516,10 +516,10 @@ def run_batch(args):
     _, _, local = dist_env()
     torch.cuda.set_device(local)
     ge.build()
-    descs = syn.c2_systems(0)
+    descs = syn.batch16_systems(0)
     ctxs, blocks, bounds, degrees, units = [], [], [], [], 0
     for d in descs:
-        prob = syn.c2_problem(d)
+        prob = syn.batch16_problem(d)
         c = g.Context(torch.cuda.current_device())
         c.set_problem(prob)
         c.set_precision(g.FP32)
@@ -565,7 +565,7 @@ def run_batch(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "16 uneven periodic systems, 8^3..14^3 cells, p in {4,5,6}, "
                                   "64..320 vectors, 8..40 atoms x 18 projectors, degree 12..24",
-                      "config": "c2", "systems": descs,
+                      "config": "batch16", "systems": descs,
                       "l2": "inputs larger than L2"},
            "batched_graph_kernels_per_step": batch.launches(),
            "tiles": [c.tile() for c in ctxs],
@@ -579,7 +579,7 @@ def run_batch(args):
 
 
 def run_backward(args):
-    """Config 3: the c1 mesh and atoms at the Gamma point, 128 vectors, degree 20: one
+    """cube16_p6_grad: the cube16_p6 mesh and atoms at the Gamma point, 128 vectors, degree 20: one
     step = FP32 forward filter + energy gradient (G_Y = 2 H Y W) + the backward of the
     filter (gbc_filter_vjp, checkpoints every 5 degrees) giving dL/dX, dL/dV_eff,
     dL/dB_xc at the quadrature points and dL/dDelta."""
@@ -594,10 +594,10 @@ def run_backward(args):
     _, _, local = dist_env()
     torch.cuda.set_device(local)
     ge.build()
-    cfg = syn.CONFIGS["c3"]
+    cfg = syn.CONFIGS["cube16_p6_grad"]
     nvec = args.nvec or cfg["nvec"]
     degree = args.degree or cfg["degree"]
-    prob = syn.config("c3", seed=0)
+    prob = syn.config("cube16_p6_grad", seed=0)
     M = prob.nnodes
     c = g.Context(torch.cuda.current_device())
     c.set_problem(prob)
@@ -648,7 +648,7 @@ def run_backward(args):
            "config": {"workload": f"16x16x16 periodic cells, p=6, nq=8 ({M:,} nodes), 64 atoms x 18 "
                                   f"SOC projectors, {nvec} vectors, degree {degree}, Gamma point; "
                                   "L = sum_i w_i y_i^H H y_i",
-                      "config": "c3", "checkpoint_every": 5},
+                      "config": "cube16_p6_grad", "checkpoint_every": 5},
            "ms_forward_filter": ms_fwd, "ms_backward": ms_bwd,
            "backward_over_forward": ms_bwd / ms_fwd,
            "backward_note": "energy gradient + filter VJP, gradients copied to the host",
@@ -721,7 +721,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbchfsi", choices=["gbchfsi", "reference"])
-    ap.add_argument("--config", default="c1")
+    ap.add_argument("--config", default="cube16_p6")
     ap.add_argument("--kpoints", type=int, default=0, help="use only the first K k-points")
     ap.add_argument("--nvec", type=int, default=0, help="override the block size (profiling runs)")
     ap.add_argument("--degree", type=int, default=0, help="override the degree (profiling runs)")
@@ -738,9 +738,9 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.config == "c2":
+    elif args.config == "batch16":
         run_batch(args)
-    elif args.config == "c3":
+    elif args.config == "cube16_p6_grad":
         run_backward(args)
     else:
         run_gpu(args)

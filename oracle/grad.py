@@ -2,7 +2,7 @@
 
 Test infrastructure only (see ``oracle/__init__``).
 
-Loss (config-3 workload): L = sum_i w_i y_i^H H y_i with Y = rho_m(M_D^-1 H) X_0
+Loss (the cube16_p6_grad workload): L = sum_i w_i y_i^H H y_i with Y = rho_m(M_D^-1 H) X_0
 (Eq. chebfilt, sigma-scaled), H from Eqs. FEHloc / FEHnloc.  Gradients use the
 convention grad = dL/dRe + i dL/dIm for complex quantities, so for a
 Hermitian form z^H A z the gradient is 2 A z.

@@ -327,19 +327,20 @@ def mp_kpoints(n1, n2, n3, box):
 
 CONFIGS = {
     # 6^3 cells, p=4, nq=6, Gamma, 4 atoms with one l=1 channel, 32 vectors, m=10, 3 cycles
-    "c0": dict(ncell=(6, 6, 6), p=4, nq=6, natoms=4, channels=P_CHANNEL, nvec=32, degree=10,
+    "cube6_p4": dict(ncell=(6, 6, 6), p=4, nq=6, natoms=4, channels=P_CHANNEL, nvec=32, degree=10,
                cycles=3, lanczos=10, kgrid=(1, 1, 1)),
     # 16^3 cells, p=6, nq=8, 64 atoms (jittered 4^3 lattice), 18 projectors, 256 vectors, m=20, 2x2x1 k
-    "c1": dict(ncell=(16, 16, 16), p=6, nq=8, lattice=(4, 4.0, 0.3), channels=SPD_CHANNELS,
+    "cube16_p6": dict(ncell=(16, 16, 16), p=6, nq=8, lattice=(4, 4.0, 0.3), channels=SPD_CHANNELS,
                nvec=256, degree=20, cycles=1, lanczos=10, kgrid=(2, 2, 1)),
-    # backward workload: c1 mesh and atoms, 128 vectors, m=20
-    "c3": dict(ncell=(16, 16, 16), p=6, nq=8, lattice=(4, 4.0, 0.3), channels=SPD_CHANNELS,
+    # backward workload: the cube16_p6 mesh and atoms, 128 vectors, m=20
+    "cube16_p6_grad": dict(ncell=(16, 16, 16), p=6, nq=8, lattice=(4, 4.0, 0.3), channels=SPD_CHANNELS,
                nvec=128, degree=20, cycles=0, lanczos=10, kgrid=(1, 1, 1)),
 }
 
 
 def config(name: str, seed: int = 0, kindex: int = 0, **over) -> Problem:
-    """Problem for a named workload (c0, c1, c3) at k-point ``kindex``."""
+    """Problem for a named workload (cube6_p4, cube16_p6, cube16_p6_grad) at k-point
+    ``kindex``."""
     c = dict(CONFIGS[name])
     c.update(over)
     h = (1.0, 1.0, 1.0)
@@ -355,7 +356,7 @@ def config(name: str, seed: int = 0, kindex: int = 0, **over) -> Problem:
                         seed=seed, name=name)
 
 
-def c2_systems(seed: int = 0):
+def batch16_systems(seed: int = 0):
     """Sixteen independent periodic systems of uneven size for the batched filter:
     8^3..14^3 cells, p in {4, 5, 6}, 64..320 vectors, 8..40 atoms with s, p, d
     projectors (18 per atom), Chebyshev degree 12..24 (seed stream 6)."""
@@ -369,8 +370,8 @@ def c2_systems(seed: int = 0):
     return out
 
 
-def c2_problem(desc) -> Problem:
-    """The Problem of one c2_systems() entry (Gamma point, 1 bohr cells)."""
+def batch16_problem(desc) -> Problem:
+    """The Problem of one batch16_systems() entry (Gamma point, 1 bohr cells)."""
     return make_problem(ncell=desc["ncell"], h=(1.0, 1.0, 1.0), p=desc["p"], nq=desc["p"] + 2,
                         periodic=(1, 1, 1), k=(0.0, 0.0, 0.0), natoms=desc["natoms"],
-                        channels=SPD_CHANNELS, seed=desc["seed"], name="c2")
+                        channels=SPD_CHANNELS, seed=desc["seed"], name="batch16")

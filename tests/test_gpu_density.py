@@ -5,7 +5,7 @@ Eqs. rho and mag) against the FP64 oracle.
   ragged vector counts (the FP32 kernel takes two vectors per CTA), padded columns
   filled with NaN (never read), zero and negative occupations;
 * the device-output form equals the host-output form bit for bit;
-* the full config-1 mesh (16^3 cells, p = 6, 884,736 nodes) on sampled cells, FP64 and
+* the full cube16_p6 mesh (16^3 cells, p = 6, 884,736 nodes) on sampled cells, FP64 and
   FP32, and there the quadrature integral sum_q w_q J rho_q = sum_n f_n x_n^H
   (H[V+1] - H[V]) x_n through the GPU's own H.X (FP64).
 
@@ -99,8 +99,8 @@ def test_density_argument_errors(g):
 
 
 @pytest.fixture(scope="module")
-def c1():
-    prob = syn.config("c1", kindex=1)
+def cube16():
+    prob = syn.config("cube16_p6", kindex=1)
     d = fe.Discretisation(prob)
     X = syn.random_block(d.mesh.nnodes, 32, 61)
     occ = np.random.default_rng(7).uniform(0.0, 1.0, 32)
@@ -111,8 +111,8 @@ def c1():
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-6)])
-def test_density_full_mesh_sampled_cells(g, c1, prec, tol):
-    prob, d, X, occ, cells, rho_o, m_o = c1
+def test_density_full_mesh_sampled_cells(g, cube16, prec, tol):
+    prob, d, X, occ, cells, rho_o, m_o = cube16
     c = g.Context(0)
     c.set_problem(prob)
     c.set_precision(prec)

@@ -1,6 +1,6 @@
 """Backward of the filter on the GPU (gbc_filter_vjp, gbc_energy_grad and the
 torch.autograd wrappers) against the FP64 oracle gradients, and a central
-finite-difference check of the full-size config-1 mesh (FP64)."""
+finite-difference check of the full-size cube16_p6 mesh (FP64)."""
 import numpy as np
 import pytest
 
@@ -89,11 +89,11 @@ def test_autograd_end_to_end(g, small):
 
 
 def test_full_size_c1_mesh_gradients_vs_fd(g):
-    """Config-1 mesh, atoms and k-point, 4 vectors, degree 20, checkpoints every
+    """cube16_p6 mesh, atoms and k-point, 4 vectors, degree 20, checkpoints every
     5: the FP64 GPU gradient agrees with central differences of the FP64 GPU loss
     along seeded directions (to the differences' own run-to-run scatter), and the
     FP32 backward agrees with the FP64 one."""
-    prob = syn.config("c1", kindex=0)
+    prob = syn.config("cube16_p6", kindex=0)
     c = g.Context(0)
     c.set_problem(prob)
     M = prob.nnodes

@@ -125,7 +125,7 @@ def test_tensor_nonlocal_filter_and_engine_errors(g):
 
 
 def test_tensor_nonlocal_long_chains_unbiased(g):
-    """Config-1 atoms (19k-node supports: projection chains of 1024 nodes, 4-14
+    """cube16_p6 atoms (19k-node supports: projection chains of 1024 nodes, 4-14
     expansion slots) with Delta scaled by 1e5 so that the nonlocal part dominates
     H X: (H X - H_loc X) from the FP32 tensor engine against the FP64 oracle's
     nonlocal apply.  The tensor core's accumulator truncates toward zero, which
@@ -133,7 +133,7 @@ def test_tensor_nonlocal_long_chains_unbiased(g):
     relative error and its systematic part (the error's component along the
     exact result)."""
     import dataclasses
-    prob = syn.config("c1", kindex=1)
+    prob = syn.config("cube16_p6", kindex=1)
     # at Delta x 1 the nonlocal part is ~2.5e-4 of the local one on random blocks
     prob = prob.with_(atoms=[dataclasses.replace(a, delta=a.delta * 1e5) for a in prob.atoms])
     d = fe.Discretisation(prob)

@@ -163,9 +163,9 @@ def test_cholgs_and_rayleigh_ritz(g, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_c0_chfsi_ritz_values(g, prec):
-    """Config-0 workload end to end: Lanczos bounds, cycle 0, 3 x (filter, CholGS, RR)."""
-    prob = syn.config("c0")
-    c = syn.CONFIGS["c0"]
+    """cube6_p4 workload end to end: Lanczos bounds, cycle 0, 3 x (filter, CholGS, RR)."""
+    prob = syn.config("cube6_p4")
+    c = syn.CONFIGS["cube6_p4"]
     d = fe.Discretisation(prob)
     M = d.mesh.nnodes
     X0 = syn.random_block(M, c["nvec"], 0)
@@ -189,9 +189,9 @@ def test_c0_chfsi_ritz_values(g, prec):
 
 
 def test_c1_full_size_sampled_rows(g):
-    """Config-1 mesh and atoms at full size (884,736 nodes, 64 atoms, 18 projectors,
+    """cube16_p6 mesh and atoms at full size (884,736 nodes, 64 atoms, 18 projectors,
     k != 0), FP64 and FP32 H.X checked on sampled rows against the oracle."""
-    prob = syn.config("c1", kindex=1)
+    prob = syn.config("cube16_p6", kindex=1)
     d = fe.Discretisation(prob)
     M = d.mesh.nnodes
     rng = np.random.default_rng(0)

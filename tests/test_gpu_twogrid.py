@@ -4,7 +4,7 @@
   periodic and Dirichlet faces, FP64 and FP32, ragged vector tiles (16 FP32 / 8 FP64 vectors
   per CTA), padded columns: NaN in the coarse padding (never read) and a sentinel in the fine
   padding (never written);
-* the full config-1 mesh (16^3 cells) from p = 5 to p = 6 on sampled cells, FP32;
+* the full cube16_p6 mesh (16^3 cells) from p = 5 to p = 6 on sampled cells, FP32;
 * argument errors, after which the contexts stay usable.
 
 Tolerances (relative to the largest value): FP64 1e-13 (three 1-D stages of <= 7 terms);
@@ -70,7 +70,7 @@ def test_prolongate_matches_oracle(g, pc, pf, per, prec):
 
 
 def test_prolongate_full_mesh_sampled_cells(g):
-    base = syn.config("c1", kindex=1).with_(p=5, nq=7, atoms=[])
+    base = syn.config("cube16_p6", kindex=1).with_(p=5, nq=7, atoms=[])
     E = base.ncells
     z = np.zeros((E, 7 ** 3))
     base = base.with_(veff=z, bx=z, by=z, bz=z)
