@@ -63,48 +63,68 @@ def _pack(rho, m):
 
 
 def scf_loop(prob, X0, v0, nelec, kT, degree, lanczos_steps, alpha, nhist, iters, eig="chfsi"):
-    """The SCF iteration of Sec. III.B.1 on one k-point with the exchange stand-in.
+    """The SCF iteration of Sec. III.B.1 on one k-point (see ``scf_loop_k``)."""
+    res, x, ritz = scf_loop_k([prob], [X0], [v0], [1.0], nelec, kT, degree, lanczos_steps, alpha,
+                              nhist, iters, eig)
+    return res, x, ritz[0]
 
-    prob.veff is the external potential and prob.bx/by/bz must be zero: the first block
-    comes from CholGS + Rayleigh-Ritz of X0 under H[V_ext] (the cycle 0 of the eigensolver).
-    Each step then builds V_eff = V_ext + V_xc and B_xc from the input densities, runs one
-    ChFSI cycle on the block carried over (Lanczos bounds from v0, the sigma-scaled filter
-    normalised at min(lambda_min, lowest Ritz value), CholGS, Rayleigh-Ritz; ``eig='dense'``
-    takes the exact lowest eigenpairs instead), forms Fermi-Dirac occupations and the output
-    densities, and mixes.  Returns (residual norms ||F(x) - x||, final input densities,
-    final Ritz values)."""
+
+def scf_loop_k(probs, X0s, v0s, kweights, nelec, kT, degree, lanczos_steps, alpha, nhist, iters,
+               eig="chfsi"):
+    """The SCF iteration of Sec. III.B.1 over k-points with the exchange stand-in.
+
+    probs[k] differ only in the k-point; their veff is the external potential and their
+    bx/by/bz must be zero: the first block of each k-point comes from CholGS + Rayleigh-Ritz
+    of X0s[k] under H[V_ext] (the cycle 0 of the eigensolver).  Each step builds V_eff =
+    V_ext + V_xc and B_xc from the input densities (the same fields at every k-point), runs
+    one ChFSI cycle per k-point on its carried-over block (Lanczos bounds from v0s[k], the
+    sigma-scaled filter normalised at min(lambda_min, lowest Ritz value), CholGS,
+    Rayleigh-Ritz; ``eig='dense'`` takes the exact lowest eigenpairs instead), forms
+    Fermi-Dirac occupations with one chemical potential over all k-points, sums the output
+    densities over k with the Brillouin-zone weights, and mixes.  Returns (residual norms
+    ||F(x) - x||, final input densities, final Ritz values [nk, nv])."""
     from . import chfsi as oc
     from . import density as od
     from . import fe
-    vext = np.asarray(prob.veff, np.float64)
-    d = fe.Discretisation(prob)
-    md = d.md
-    nv = X0.shape[2]
-    X = oc.cholgs(X0, md)
-    ritz, X, _ = oc.rayleigh_ritz(d.apply_h, X)
-    f, _ = od.fermi_occupations(ritz[None], [1.0], nelec, kT)
-    x_in = _pack(*od.densities(d, X, f[0]))
-    W = d.tab.W
+    nk = len(probs)
+    w = np.asarray(kweights, np.float64)
+    vext = np.asarray(probs[0].veff, np.float64)
+    ds = [fe.Discretisation(pr) for pr in probs]
+    md = ds[0].md
+    nv = X0s[0].shape[2]
+    Xs, ritz = [], []
+    for d, X0 in zip(ds, X0s):
+        r, X, _ = oc.rayleigh_ritz(d.apply_h, oc.cholgs(X0, md))
+        Xs.append(X)
+        ritz.append(r)
+
+    def densities(ds, ritz):
+        f, _ = od.fermi_occupations(np.array(ritz), w, nelec, kT)
+        return sum(w[k] * _pack(*od.densities(ds[k], Xs[k], f[k])) for k in range(nk))
+
+    x_in = densities(ds, ritz)
+    W = ds[0].tab.W
     xs, fs, res = [], [], []
     for _ in range(iters):
         _, V, B = lsda_exchange(x_in[:, 0], np.moveaxis(x_in[:, 1:], 1, 0))
-        d = fe.Discretisation(prob.with_(veff=vext + V, bx=B[0], by=B[1], bz=B[2]))
-        if eig == "chfsi":
-            def apply_ht(Z, d=d):
-                return d.apply_h(Z) / md[:, None, None]
-            lo, hi = oc.lanczos_bounds(apply_ht, md, v0, lanczos_steps)
-            X = oc.cheb_filter(apply_ht, X, degree, float(ritz[-1]), hi, min(lo, float(ritz[0])))
-            X = oc.cholgs(X, md)
-            ritz, X, _ = oc.rayleigh_ritz(d.apply_h, X)
-        else:                                    # exact eigenpairs of M_D^-1/2 H M_D^-1/2
-            dm = np.repeat(1.0 / np.sqrt(md), 2)
-            H = d.dense_h()
-            w, Q = np.linalg.eigh(dm[:, None] * (0.5 * (H + H.conj().T)) * dm[None, :])
-            ritz = w[:nv]
-            X = (np.repeat(1.0 / np.sqrt(md), 2)[:, None] * Q[:, :nv]).reshape(-1, 2, nv)
-        f, _ = od.fermi_occupations(ritz[None], [1.0], nelec, kT)
-        x_out = _pack(*od.densities(d, X, f[0]))
+        ds = [fe.Discretisation(pr.with_(veff=vext + V, bx=B[0], by=B[1], bz=B[2]))
+              for pr in probs]
+        for k, d in enumerate(ds):
+            if eig == "chfsi":
+                def apply_ht(Z, d=d):
+                    return d.apply_h(Z) / md[:, None, None]
+                lo, hi = oc.lanczos_bounds(apply_ht, md, v0s[k], lanczos_steps)
+                X = oc.cheb_filter(apply_ht, Xs[k], degree, float(ritz[k][-1]), hi,
+                                   min(lo, float(ritz[k][0])))
+                ritz[k], Xs[k], _ = oc.rayleigh_ritz(d.apply_h, oc.cholgs(X, md))
+            else:                                # exact eigenpairs of M_D^-1/2 H M_D^-1/2
+                dm = np.repeat(1.0 / np.sqrt(md), 2)
+                H = d.dense_h()
+                ev, Q = np.linalg.eigh(dm[:, None] * (0.5 * (H + H.conj().T)) * dm[None, :])
+                ritz[k] = ev[:nv]
+                Xs[k] = (dm[:, None] * Q[:, :nv]).reshape(-1, 2, nv)
+        x_out = densities(ds, ritz)
         xs, fs = (xs + [x_in])[-nhist:], (fs + [x_out])[-nhist:]
         res.append(np.sqrt(inner(W, x_out - x_in, x_out - x_in)))
         x_in, _ = anderson(W, xs, [b - a for a, b in zip(xs, fs)], alpha)
-    return np.array(res), x_in, ritz
+    return np.array(res), x_in, np.array(ritz)

@@ -118,3 +118,39 @@ def test_scf_loop_reaches_the_eigensolver_independent_fixed_point():
     assert r_c[-1] < 1e-7 * r_c[0] and r_d[-1] < 1e-8 * r_d[0]
     np.testing.assert_allclose(x_c, x_d, rtol=0, atol=1e-7 * np.abs(x_d).max())
     np.testing.assert_allclose(e_c[:3], e_d[:3], rtol=0, atol=1e-8)
+
+
+def _two_atom_problem(k=(0.0, 0.0, 0.0)):
+    z = np.zeros((8, 4 ** 3))
+    return syn.make_problem(ncell=(2, 2, 2), h=(1.0, 1.0, 1.0), p=2, k=k, natoms=2, rc=1.0,
+                            seed=9, well_depth=3.0, bmax=0.0).with_(bx=z, by=z, bz=z)
+
+
+def test_scf_k_loop_weights():
+    """Two copies of one k-point with weights 0.3 / 0.7 reproduce the single-k loop."""
+    prob = _two_atom_problem()
+    M = prob.nnodes
+    X0, v0 = syn.random_block(M, 12, 3), syn.random_start(M, 3)
+    args = dict(nelec=3.0, kT=0.05, degree=16, lanczos_steps=12, alpha=0.5, nhist=4, iters=6)
+    r1, x1, e1 = scf.scf_loop(prob, X0, v0, **args)
+    r2, x2, e2 = scf.scf_loop_k([prob, prob], [X0, X0], [v0, v0], [0.3, 0.7], **args)
+    # 0.3 f + 0.7 f rounds differently from f, and each step's filter amplifies rounding-level
+    # differences of its input (~1e-10 relative after 6 steps): equal up to rounding
+    np.testing.assert_allclose(r2, r1, rtol=1e-8)
+    np.testing.assert_allclose(x2, x1, rtol=0, atol=1e-9 * np.abs(x1).max())
+    np.testing.assert_allclose(e2[1], e1, rtol=1e-8)
+
+
+def test_scf_k_loop_eigensolver_independent():
+    """Two distinct k-points: one ChFSI cycle per step and exact eigenpairs reach the same
+    Brillouin-zone-summed fixed point."""
+    probs = [_two_atom_problem((0.3, 0.0, 0.0)), _two_atom_problem((-0.2, 0.4, 0.1))]
+    M = probs[0].nnodes
+    X0s = [syn.random_block(M, 12, 3 + i) for i in range(2)]
+    v0s = [syn.random_start(M, 3 + i) for i in range(2)]
+    args = dict(nelec=3.0, kT=0.05, degree=16, lanczos_steps=12, alpha=0.5, nhist=4, iters=30)
+    r_c, x_c, e_c = scf.scf_loop_k(probs, X0s, v0s, [0.5, 0.5], eig="chfsi", **args)
+    r_d, x_d, e_d = scf.scf_loop_k(probs, X0s, v0s, [0.5, 0.5], eig="dense", **args)
+    assert r_c[-1] < 1e-7 * r_c[0] and r_d[-1] < 1e-8 * r_d[0]
+    np.testing.assert_allclose(x_c, x_d, rtol=0, atol=1e-7 * np.abs(x_d).max())
+    np.testing.assert_allclose(e_c[:, :3], e_d[:, :3], rtol=0, atol=1e-8)
