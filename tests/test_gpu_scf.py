@@ -115,3 +115,31 @@ def test_scf_loop_matches_oracle(g):
     np.testing.assert_allclose(out["dens"].cpu().numpy(), x_o, rtol=0, atol=1e-7 * np.abs(x_o).max())
     np.testing.assert_allclose(out["ritz"][:3], e_o[:3], rtol=0, atol=1e-8)
     c.close()
+
+
+def test_scf_loop_two_kpoints_matches_oracle(g):
+    """Two k-points in one process: common chemical potential, Brillouin-zone-summed
+    densities (accumulate mode), the same fields at both k-points."""
+    from paper_2410_02754_gb300 import scf
+    z = np.zeros((8, 4 ** 3))
+    probs = [syn.make_problem(ncell=(2, 2, 2), h=(1.0, 1.0, 1.0), p=2, k=k, natoms=2, rc=1.0,
+                              seed=9, well_depth=3.0, bmax=0.0).with_(bx=z, by=z, bz=z)
+             for k in ((0.3, 0.0, 0.0), (-0.2, 0.4, 0.1))]
+    M = probs[0].nnodes
+    X0s = [syn.random_block(M, 12, 3 + i) for i in range(2)]
+    v0s = [syn.random_start(M, 3 + i) for i in range(2)]
+    args = dict(nelec=3.0, kT=0.05, degree=16, lanczos_steps=12, alpha=0.5, nhist=4, iters=20)
+    r_o, x_o, e_o = osc.scf_loop_k(probs, X0s, v0s, [0.5, 0.5], **args)
+    ctxs = []
+    for p in probs:
+        c = g.Context(0)
+        c.set_problem(p)
+        ctxs.append(c)
+    out = scf.scf_loop_k(ctxs, [torch.from_numpy(X).cuda() for X in X0s],
+                         torch.from_numpy(np.ascontiguousarray(probs[0].veff)).cuda(),
+                         [torch.from_numpy(v).cuda() for v in v0s], [0.5, 0.5], **args)
+    np.testing.assert_allclose(out["res"][:8], r_o[:8], rtol=1e-6)
+    np.testing.assert_allclose(out["dens"].cpu().numpy(), x_o, rtol=0, atol=1e-7 * np.abs(x_o).max())
+    np.testing.assert_allclose(out["ritz"][:, :3], e_o[:, :3], rtol=0, atol=1e-8)
+    for c in ctxs:
+        c.close()
