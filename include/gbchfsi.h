@@ -51,8 +51,12 @@ typedef enum {
 
 typedef enum {
   GBC_FP64 = 0,          /* complex128 blocks, FP64 arithmetic everywhere               */
-  GBC_FP32 = 1           /* complex64 blocks, FP32 arithmetic in H.X and the filter;
+  GBC_FP32 = 1,          /* complex64 blocks, FP32 arithmetic in H.X and the filter;
                             Gram matrices accumulated in FP64                           */
+  GBC_TF32 = 2,          /* reserved: cell apply on the TF32 tensor cores (not built;
+                            gbc_set_precision returns GBC_EUNSUPPORTED)                 */
+  GBC_BF16X3 = 3         /* reserved: cell apply in split BF16 on the tensor cores (not
+                            built; gbc_set_precision returns GBC_EUNSUPPORTED)          */
 } gbc_precision;
 
 /* ---- context ----------------------------------------------------------- */
@@ -126,8 +130,10 @@ gbc_status gbc_get_nonlocal_engine(const gbc_ctx* ctx, int* engine);
  * for a CUDA error, else GBC_OK.  Clears the recorded flag. */
 gbc_status gbc_sync_status(gbc_ctx* ctx, void* stream);
 
-/* Number M of free FE nodes (spinor DOFs per vector = 2M). */
+/* Number M of free FE nodes (spinor DOFs per vector = 2M).  gbc_get_ndof is the
+ * same call under a second name. */
 gbc_status gbc_get_nnodes(const gbc_ctx* ctx, long long* nnodes);
+gbc_status gbc_get_ndof(const gbc_ctx* ctx, long long* nnodes);
 
 /* Copy M_D (length M, FP64) to host memory ``md``.  Synchronous. */
 gbc_status gbc_get_mass(gbc_ctx* ctx, double* md);
@@ -202,6 +208,10 @@ gbc_status gbc_rayleigh_ritz(gbc_ctx* ctx, void* X, int nvec, int ldx, double* r
 gbc_status gbc_filter_vjp(gbc_ctx* ctx, const void* X0, const void* GY, void* GX, double* gV,
                           double* gB, double* gDelta, int nvec, int ldx, int degree, double lT,
                           double lmax, double lmin, int ckpt_every, void* stream);
+/* The same call under a second name. */
+gbc_status gbc_filter_backward(gbc_ctx* ctx, const void* X0, const void* GY, void* GX, double* gV,
+                               double* gB, double* gDelta, int nvec, int ldx, int degree,
+                               double lT, double lmax, double lmin, int ckpt_every, void* stream);
 
 /* L = sum_i w_i y_i^H H y_i for the block Y, with GY = 2 H Y diag(w) (device
  * block, written) and the gradients of L at fixed Y with respect to V_eff, B_xc

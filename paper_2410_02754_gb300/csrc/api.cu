@@ -514,6 +514,8 @@ gbc_status gbc_set_projectors(gbc_ctx* c, int natoms, const int* npj, const int*
 
 gbc_status gbc_set_precision(gbc_ctx* c, gbc_precision prec) {
   if (!c) return GBC_EINVAL;
+  if (prec == GBC_TF32 || prec == GBC_BF16X3)
+    return gbc_fail(c, GBC_EUNSUPPORTED, "tensor-core cell apply precisions are not built");
   if (prec != GBC_FP64 && prec != GBC_FP32) return gbc_fail(c, GBC_EUNSUPPORTED, "unknown precision");
   c->prec = prec;
   return GBC_OK;
@@ -553,6 +555,8 @@ gbc_status gbc_get_nnodes(const gbc_ctx* c, long long* nnodes) {
   *nnodes = c->mesh.M;
   return GBC_OK;
 }
+
+gbc_status gbc_get_ndof(const gbc_ctx* c, long long* nnodes) { return gbc_get_nnodes(c, nnodes); }
 
 gbc_status gbc_get_mass(gbc_ctx* c, double* md) {
   if (!c) return GBC_EINVAL;

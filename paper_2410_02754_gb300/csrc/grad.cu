@@ -388,6 +388,13 @@ gbc_status gbc_filter_vjp(gbc_ctx* c, const void* X0, const void* GY, void* GX, 
                              nvec, ldx, degree, lT, lmax, lmin, ckpt_every, s);
 }
 
+gbc_status gbc_filter_backward(gbc_ctx* c, const void* X0, const void* GY, void* GX, double* gV,
+                               double* gB, double* gDelta, int nvec, int ldx, int degree,
+                               double lT, double lmax, double lmin, int ckpt_every, void* stream) {
+  return gbc_filter_vjp(c, X0, GY, GX, gV, gB, gDelta, nvec, ldx, degree, lT, lmax, lmin,
+                        ckpt_every, stream);
+}
+
 gbc_status gbc_energy_grad(gbc_ctx* c, const void* Y, const double* w, void* GY, double* loss,
                            double* gV, double* gB, double* gDelta, int nvec, int ldx,
                            void* stream) {

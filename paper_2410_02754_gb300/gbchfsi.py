@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgbchfsi.so")
 
 FP64, FP32 = 0, 1
+TF32, BF16X3 = 2, 3          # reserved: tensor-core cell apply, not built (GBC_EUNSUPPORTED)
 STATUS = {0: "GBC_OK", 1: "GBC_EINVAL", 2: "GBC_ENOMEM", 3: "GBC_ECUDA", 4: "GBC_ESTATE",
           5: "GBC_ENOTPD", 6: "GBC_ETIMEOUT", 7: "GBC_EUNSUPPORTED"}
 
@@ -32,7 +33,8 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_get_tile", "gbc_filter_vjp", "gbc_energy_grad", "gbc_set_delta",
            "gbc_tc_gemm_nt", "gbc_tc_wait_selftest", "gbc_set_nonlocal_engine", "gbc_get_nonlocal_engine",
            "gbc_sync_status", "gbc_density", "gbc_density_dev", "gbc_fermi_occupations",
-           "gbc_prolongate", "gbc_scf_fields", "gbc_anderson_mix"]
+           "gbc_prolongate", "gbc_scf_fields", "gbc_anderson_mix", "gbc_get_ndof",
+           "gbc_filter_backward"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -89,6 +91,8 @@ def load_library(path: str = LIB_PATH):
         "gbc_density_dev": ([P, V, V, V, I, I, I, V], I),
         "gbc_fermi_occupations": ([DP, DP, I, I, D, D, DP, DP], I),
         "gbc_prolongate": ([P, P, V, I, V, I, I, V], I),
+        "gbc_get_ndof": ([P, ct.POINTER(ct.c_longlong)], I),
+        "gbc_filter_backward": ([P, V, V, V, DP, DP, DP, I, I, I, D, D, D, I, V], I),
         "gbc_scf_fields": ([P, V, V, V, V], I),
         "gbc_anderson_mix": ([P, ct.POINTER(V), ct.POINTER(V), I, D, V, DP, DP, V], I),
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
