@@ -1,4 +1,4 @@
-"""PIN-11: the oracle's densities rho and m at the Gauss points (Eqs. rho, mag) against
+"""PIN-12: the oracle's densities rho and m at the Gauss points (Eqs. rho, mag) against
 what the mathematics fixes independently of its formula:
 
 * polynomial reproduction + the Bloch sphere: nodal values X = (a_n, b_n) phi(r_I) of a

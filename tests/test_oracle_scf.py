@@ -1,4 +1,4 @@
-"""PIN-13: the oracle's SCF pieces against what the mathematics fixes.
+"""PIN-14: the oracle's SCF pieces against what the mathematics fixes.
 
 * exchange stand-in: m = 0 gives Dirac exchange -(3/4)(3/pi)^(1/3) rho^(4/3) and
   V = -(3/pi)^(1/3) rho^(1/3); |m| = rho gives -(3/4)(6/pi)^(1/3) rho^(4/3); V and B equal

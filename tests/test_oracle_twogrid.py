@@ -1,4 +1,4 @@
-"""PIN-12: the oracle's two-grid transfer (order p_c -> p_f on the same mesh, Eq.
+"""PIN-13: the oracle's two-grid transfer (order p_c -> p_f on the same mesh, Eq.
 FEWfnsCMesh) against what the mathematics fixes:
 
 * polynomial reproduction: nodal values of a polynomial of degree <= p_c in each coordinate
