@@ -201,13 +201,16 @@ def _support(pos, ncell, h, periodic, rc):
 def make_problem(ncell=(2, 2, 2), h=(1.0, 1.0, 1.0), p=2, nq=None, periodic=(1, 1, 1),
                  k=(0.0, 0.0, 0.0), atom_pos=None, natoms=0, channels=((0.5, 1),),
                  well_depth=2.0, well_width=0.8, bmax=0.1, nmodes=3, rc=2.0,
-                 delta_std=0.1, seed=0, name="") -> Problem:
+                 delta_std=0.1, seed=0, name="", well_cutoff=None) -> Problem:
     """Draw one synthetic problem.
 
     channels: sequence of (sigma, l) radial channels; each contributes 2l+1
       projectors r^l exp(-r^2/(2 sigma^2)) Y_lm, L2-normalised on [0, rc].
     atom_pos: explicit positions (natoms, 3) or None to draw ``natoms``
       uniformly in the box (seed stream 1).
+    well_cutoff: None sums every well over every point; a radius (bohr) sums each
+      well only over the cells within that distance of the atom (minimum image),
+      for meshes where atoms x points is too large to sum in full.
     """
     ncell = tuple(int(n) for n in ncell)
     h = tuple(float(x) for x in h)
@@ -227,7 +230,7 @@ def make_problem(ncell=(2, 2, 2), h=(1.0, 1.0, 1.0), p=2, nq=None, periodic=(1, 
     # ---- V_eff: Gaussian wells (image sum for small boxes, minimum image otherwise)
     V = np.zeros(rq.shape[0])
     small = box[per].size and box[per].min() < 8 * well_width
-    for R in atom_pos:
+    for R in (atom_pos if well_cutoff is None else []):
         if small:
             for iz in ([-1, 0, 1] if per[2] else [0]):
                 for iy in ([-1, 0, 1] if per[1] else [0]):
@@ -238,6 +241,15 @@ def make_problem(ncell=(2, 2, 2), h=(1.0, 1.0, 1.0), p=2, nq=None, periodic=(1, 
             d = rq - R
             d[:, per] -= box[per] * np.round(d[:, per] / box[per])
             V -= well_depth * np.exp(-(d * d).sum(-1) / (2 * well_width ** 2))
+
+    if well_cutoff is not None:
+        nq3 = nq ** 3
+        for R in atom_pos:
+            sc, si = _support(R, ncell, h, periodic, well_cutoff)
+            for c, L in zip(sc, si):
+                pts = slice(int(c) * nq3, (int(c) + 1) * nq3)
+                d = rq[pts] - R - L * box
+                V[pts] -= well_depth * np.exp(-(d * d).sum(-1) / (2 * well_width ** 2))
 
     # ---- B_xc: a few low-frequency Fourier modes, rescaled to max |B| = bmax
     r2 = _rng(seed, 2)
@@ -307,9 +319,14 @@ SPD_CHANNELS = ((0.5, 0), (0.65, 0), (0.5, 1), (0.65, 1), (0.5, 2), (0.65, 2))  
 P_CHANNEL = ((0.5, 1),)                                                            # 3 projectors
 
 
-def _jittered_lattice(n, spacing, jitter, seed):
+def _jittered_lattice(n, spacing, jitter, seed, origin=(0.0, 0.0, 0.0)):
+    """Sites of an n (int or 3 ints) lattice of the given spacing (number or 3 numbers)
+    from ``origin``, cell-centred, each moved by uniform(-jitter, jitter) (seed stream 1)."""
     r = _rng(seed, 1)
-    g = (np.stack(np.meshgrid(*[np.arange(n)] * 3, indexing="ij"), -1).reshape(-1, 3) + 0.5) * spacing
+    n3 = (n, n, n) if np.isscalar(n) else tuple(n)
+    sp = np.broadcast_to(np.asarray(spacing, np.float64), (3,))
+    g = np.stack(np.meshgrid(*[np.arange(m) for m in n3], indexing="ij"), -1).reshape(-1, 3)
+    g = (g + 0.5) * sp + np.asarray(origin, np.float64)
     return g + r.uniform(-jitter, jitter, g.shape)
 
 
@@ -335,12 +352,20 @@ CONFIGS = {
     # backward workload: the cube16_p6 mesh and atoms, 128 vectors, m=20
     "cube16_p6_grad": dict(ncell=(16, 16, 16), p=6, nq=8, lattice=(4, 4.0, 0.3), channels=SPD_CHANNELS,
                nvec=128, degree=20, cycles=0, lanczos=10, kgrid=(1, 1, 1)),
+    # semi-periodic slab: 40x40x20 cells (240x240x119 = 6,854,400 free nodes), p=6, periodic in
+    # x and y, Dirichlet in z with 4 vacuum cells on each side; 640 atoms on a jittered
+    # 16x8x5 lattice inside the slab (z in [4, 16] bohr); 20,000 states filtered in blocks of
+    # 256 at m=30, Gamma; wells summed within 6 widths of each atom
+    "slab40_p6": dict(ncell=(40, 40, 20), p=6, nq=8, periodic=(1, 1, 0),
+                      slab_lattice=((16, 8, 5), (2.5, 5.0, 2.4), 0.3, (0.0, 0.0, 4.0)),
+                      channels=SPD_CHANNELS, nvec=256, degree=30, nstates=20000, cycles=1,
+                      lanczos=10, kgrid=(1, 1, 1), well_cutoff=4.8),
 }
 
 
 def config(name: str, seed: int = 0, kindex: int = 0, **over) -> Problem:
-    """Problem for a named workload (cube6_p4, cube16_p6, cube16_p6_grad) at k-point
-    ``kindex``."""
+    """Problem for a named workload (cube6_p4, cube16_p6, cube16_p6_grad, slab40_p6) at
+    k-point ``kindex``."""
     c = dict(CONFIGS[name])
     c.update(over)
     h = (1.0, 1.0, 1.0)
@@ -351,9 +376,13 @@ def config(name: str, seed: int = 0, kindex: int = 0, **over) -> Problem:
     if "lattice" in c:
         n, sp, jit = c["lattice"]
         pos = _jittered_lattice(n, sp, jit, seed)
-    return make_problem(ncell=c["ncell"], h=h, p=c["p"], nq=c["nq"], periodic=(1, 1, 1),
-                        k=ks[kindex], atom_pos=pos, natoms=natoms, channels=c["channels"],
-                        seed=seed, name=name)
+    if "slab_lattice" in c:
+        n, sp, jit, origin = c["slab_lattice"]
+        pos = _jittered_lattice(n, sp, jit, seed, origin)
+    return make_problem(ncell=c["ncell"], h=h, p=c["p"], nq=c["nq"],
+                        periodic=c.get("periodic", (1, 1, 1)), k=ks[kindex], atom_pos=pos,
+                        natoms=natoms, channels=c["channels"], seed=seed, name=name,
+                        well_cutoff=c.get("well_cutoff"))
 
 
 def batch16_systems(seed: int = 0):
