@@ -246,7 +246,8 @@ gbc_status gbc_set_delta(gbc_ctx* ctx, const double* delta);
  * built (see gbc_apply_h_noalloc).
  * gbc_density: occ, rho and mag are HOST arrays; rho [E][nq^3] and mag
  * [3][E][nq^3] (layout as gbc_set_fields; mag may be NULL) are written.
- * Synchronous; uses library workspace. */
+ * Synchronous; uses library workspace.
+ * Device arguments that are not device (or managed) memory: GBC_EINVAL. */
 gbc_status gbc_density_dev(gbc_ctx* ctx, const void* X, const double* occ, double* out, int nvec,
                            int ldx, int accumulate, void* stream);
 

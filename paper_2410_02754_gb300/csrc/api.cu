@@ -25,6 +25,16 @@ gbc_status gbc_cuda_fail(gbc_ctx* c, cudaError_t e, const char* where) {
   return gbc_fail(c, e == cudaErrorMemoryAllocation ? GBC_ENOMEM : GBC_ECUDA, m);
 }
 
+bool gbc_is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // clear the sticky-free error of an unknown pointer
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 gbc_status gbc_ensure_work(gbc_ctx* c, int slot, size_t bytes) {
   if (c->work_bytes[slot] >= bytes) return GBC_OK;
   if (c->work[slot]) cudaFree(c->work[slot]);

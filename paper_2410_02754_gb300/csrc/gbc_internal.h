@@ -190,6 +190,9 @@ gbc_status gbc_cuda_fail(gbc_ctx* c, cudaError_t e, const char* where);
 gbc_status gbc_ensure_work(gbc_ctx* c, int slot, size_t bytes);
 gbc_status gbc_ensure_small(gbc_ctx* c, size_t bytes);
 gbc_status gbc_prepare(gbc_ctx* c);    // (re)builds fields / projector tables if dirty
+// true if p is device (or managed) memory that kernels may dereference; a host
+// pointer passed where device memory is required is refused instead of faulting
+bool gbc_is_device_ptr(const void* p);
 gbc_status gbc_apply_h_dev(gbc_ctx* c, const void* X, void* Y, int nvec, int ldx, bool zero,
                            cudaStream_t s);
 

@@ -347,6 +347,8 @@ gbc_status gbc_density_dev(gbc_ctx* c, const void* X, const double* occ, double*
                            int ldx, int accumulate, void* stream) {
   if (!c) return GBC_EINVAL;
   GBC_TRY(density_check(c, X, occ, out, nvec, ldx));
+  if (!gbc_is_device_ptr(X) || !gbc_is_device_ptr(occ) || !gbc_is_device_ptr(out))
+    return gbc_fail(c, GBC_EINVAL, "X, occ and out must be device memory");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->prec == GBC_FP64)
     GBC_CU(c, density_t<double>(c, (const double2*)X, occ, out, nvec, ldx, accumulate, s));
@@ -359,6 +361,7 @@ gbc_status gbc_density(gbc_ctx* c, const void* X, const double* occ, double* rho
                        int nvec, int ldx, void* stream) {
   if (!c) return GBC_EINVAL;
   GBC_TRY(density_check(c, X, occ, rho, nvec, ldx));
+  if (!gbc_is_device_ptr(X)) return gbc_fail(c, GBC_EINVAL, "X must be device memory");
   cudaStream_t s = (cudaStream_t)stream;
   GradScratch gs;
   GBC_TRY(grad_scratch(c, nvec, &gs));

@@ -122,6 +122,8 @@ gbc_status gbc_scf_fields(gbc_ctx* c, const double* dens, const double* vext, do
   if (!c) return GBC_EINVAL;
   if (!dens || !vext) return gbc_fail(c, GBC_EINVAL, "null argument");
   if (!c->mesh_set) return gbc_fail(c, GBC_ESTATE, "gbc_set_mesh first");
+  if (!gbc_is_device_ptr(dens) || !gbc_is_device_ptr(vext) || (exc && !gbc_is_device_ptr(exc)))
+    return gbc_fail(c, GBC_EINVAL, "dens, vext and exc must be device memory");
   GBC_CU(c, cudaSetDevice(c->dev));
   const long long nq3 = (long long)c->nq * c->nq * c->nq;
   const long long n = (long long)c->mesh.E * nq3;
@@ -142,12 +144,14 @@ gbc_status gbc_anderson_mix(gbc_ctx* c, const double* const* xin, const double* 
                             double* resnorm, void* stream) {
   if (!c) return GBC_EINVAL;
   if (!xin || !xout || !xnext) return gbc_fail(c, GBC_EINVAL, "null argument");
+  if (!gbc_is_device_ptr(xnext)) return gbc_fail(c, GBC_EINVAL, "xnext must be device memory");
   if (nhist < 1 || nhist > kMaxHist) return gbc_fail(c, GBC_EINVAL, "need 1 <= nhist <= 8");
   if (!(alpha > 0.0) || !std::isfinite(alpha)) return gbc_fail(c, GBC_EINVAL, "alpha > 0 required");
   if (!c->mesh_set) return gbc_fail(c, GBC_ESTATE, "gbc_set_mesh first");
   Hist h{};
   for (int j = 0; j < nhist; ++j) {
-    if (!xin[j] || !xout[j]) return gbc_fail(c, GBC_EINVAL, "null history entry");
+    if (!gbc_is_device_ptr(xin[j]) || !gbc_is_device_ptr(xout[j]))
+      return gbc_fail(c, GBC_EINVAL, "history entries must be device memory");
     h.x[j] = xin[j];
     h.f[j] = xout[j];
   }

@@ -161,6 +161,8 @@ extern "C" gbc_status gbc_prolongate(gbc_ctx* coarse, gbc_ctx* fine, const void*
   if (!coarse || !fine) return GBC_EINVAL;
   if (!Xc || !Xf) return gbc_fail(fine, GBC_EINVAL, "null block pointer");
   if (Xc == Xf) return gbc_fail(fine, GBC_EINVAL, "Xc and Xf must be distinct");
+  if (!gbc_is_device_ptr(Xc) || !gbc_is_device_ptr(Xf))
+    return gbc_fail(fine, GBC_EINVAL, "Xc and Xf must be device memory");
   if (nvec < 1 || ldxc < nvec || ldxf < nvec)
     return gbc_fail(fine, GBC_EINVAL, "need 1 <= nvec <= ldxc, ldxf");
   if (!coarse->mesh_set || !fine->mesh_set) return gbc_fail(fine, GBC_ESTATE, "mesh not set");
