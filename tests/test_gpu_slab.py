@@ -49,11 +49,18 @@ def slab():
     return prob, X, nodes, ref
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
-def test_slab_hx_sampled_rows(g, slab, prec, tol):
-    prob, X, nodes, ref = slab
+@pytest.fixture(scope="module")
+def slab_ctx(g, slab):
     c = g.Context(0)
-    c.set_problem(prob)
+    c.set_problem(slab[0])            # 640 atoms, 4 GB of projector values: set once
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_slab_hx_sampled_rows(g, slab, slab_ctx, prec, tol):
+    prob, X, nodes, ref = slab
+    c = slab_ctx
     c.set_precision(prec)
     dt = torch.complex128 if prec == 0 else torch.complex64
     Xd = torch.from_numpy(X).to(dt).cuda()
@@ -64,4 +71,3 @@ def test_slab_hx_sampled_rows(g, slab, prec, tol):
     del Xd, Yd
     err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
     assert err < tol, err
-    c.close()
