@@ -848,6 +848,11 @@ def run_reference(args):
     if rank != 0:
         return
     import synthetic as syn
+    if args.config not in syn.CONFIGS:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"the oracle arm times single-problem workloads; {args.config} is not one"}),
+              flush=True)
+        return
     cfg = syn.CONFIGS[args.config]
     prob = syn.config(args.config, seed=0)
     ks = syn.mp_kpoints(*cfg["kgrid"], prob.box)
