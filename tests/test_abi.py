@@ -54,3 +54,18 @@ def test_product_path_does_not_reach_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"\b(import|from)\s+(oracle|synthetic)\b", txt), f
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as pedantic C99 (no C++ types cross the ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "h.c"
+    src.write_text('#include "gbchfsi.h"\nint main(void) { return 0; }\n')
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-fsyntax-only", "-I" + inc, str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
