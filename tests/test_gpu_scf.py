@@ -37,7 +37,8 @@ def rand_dens(E, q, seed):
     m = rng.normal(size=(3, E, q))
     m *= (rng.uniform(0.0, 0.9, (E, q)) * rho / np.sqrt((m * m).sum(0)))[None]
     m[:, 0, :3] = 0.0                                     # a few unpolarised points
-    return np.concatenate([rho[:, None], np.moveaxis(m, 0, 1)], 1)
+    # [E, 4, q] in C order: the binding takes contiguous device arrays only
+    return np.ascontiguousarray(np.concatenate([rho[:, None], np.moveaxis(m, 0, 1)], 1))
 
 
 def test_scf_fields_match_oracle(g):
