@@ -77,6 +77,8 @@ extern "C" gbc_status gbc_apply_h_noalloc(gbc_ctx* c, const void* X, void* Y, in
   if (!c) return GBC_EINVAL;
   if (!X || !Y) return gbc_fail(c, GBC_EINVAL, "null block pointer");
   if (X == Y) return gbc_fail(c, GBC_EINVAL, "X and Y must be distinct");
+  if (!gbc_is_device_ptr(X) || !gbc_is_device_ptr(Y))
+    return gbc_fail(c, GBC_EINVAL, "gbc_apply_h_noalloc: X and Y must be device memory");
   if (nvec < 0 || ldx < 1 || nvec > ldx) return gbc_fail(c, GBC_EINVAL, "need 0 <= nvec <= ldx, ldx >= 1");
   if (!c->mesh_set || !c->fields_set)
     return gbc_fail(c, GBC_ESTATE, "gbc_apply_h_noalloc: set mesh and fields first");
