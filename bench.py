@@ -178,6 +178,63 @@ def hbm_peak():
         return 6800.0, "of fallback (6.8 TB/s)"
 
 
+def CELL_TRAFFIC(nvec):
+    """DRAM bytes of one fused-recurrence cell-apply launch at ``nvec`` vectors on the
+    cube16_p6 mesh, scaled from the ncu capture at 32 vectors (profiles/), or None."""
+    per32 = CELL_TRAFFIC_32
+    if per32 is None:
+        return None, "no ncu capture of this kernel version"
+    return per32 * nvec / 32, "ncu capture at 32 vectors (fused recurrence mode) scaled by vectors"
+
+
+CELL_TRAFFIC_32 = None
+
+
+def tc_cell_leg(g, prob, k, X, nvec, peaks, simt_ms):
+    """Time the TF32 and BF16x3 cell apply (tcgen05 GEMMs) on one H.X of X."""
+    import torch
+    np3, nq3 = (prob.p + 1) ** 3, prob.nq ** 3
+    pad = lambda n: -(-n // 64) * 64
+    QP, NPP = pad(nq3), pad(np3)
+    rows = prob.ncells * 4 * nvec
+    dense = 2.0 * rows * (QP * NPP + NPP * (QP + 2 * NPP))     # the two GEMMs as computed
+    res = {"simt_fp32_ms": round(simt_ms, 3),
+           "flops_dense_per_launch": dense,
+           "how": "one H.X of the k-point-0 block (3 launches after one warm-up, CUDA events "
+                  "of the cell-apply family); rows = cells x spins x vectors x re/im; GEMM 1 "
+                  "interpolation (K = n_p^3), GEMM 2 testing + kinetic (K = n_q^3 + 2 n_p^3)"}
+    Yref = torch.empty_like(X)
+    c = g.Context(torch.cuda.current_device())
+    c.set_problem(prob.with_(k=k))
+    c.set_precision(g.FP32)
+    c.apply_h(X, Yref)
+    for name, prec, passes, pk in (("tf32", 2, 1, "tf32"), ("bf16x3", 3, 3, "bf16")):
+        c.set_precision(prec)
+        Y = torch.empty_like(X)
+        c.apply_h(X, Y)
+        c.sync_status()
+        c.set_timing(True)
+        for _ in range(3):
+            c.apply_h(X, Y)
+        t = c.timing()
+        c.set_timing(False)
+        c.sync_status()
+        ms = t["hx_local"][0] / t["hx_local"][1]
+        err = float(((Y - Yref).abs().pow(2).sum() / Yref.abs().pow(2).sum()).sqrt())
+        peak = peaks.get(pk)
+        ach = dense * passes / (ms / 1e3) / 1e12
+        res[name] = {"ms": round(ms, 3), "tensor_tflops": round(ach, 1),
+                     "frac_tensor": round(ach / peak, 4) if isinstance(peak, float) else None,
+                     "peak_tflops": peak, "rel_diff_vs_fp32": err,
+                     "over_simt": round(ms / simt_ms, 3)}
+        del Y
+    c.close()
+    best = min(("simt_fp32", simt_ms), ("tf32", res["tf32"]["ms"]), ("bf16x3", res["bf16x3"]["ms"]),
+               key=lambda x: x[1])
+    res["fastest"] = best[0]
+    return res
+
+
 def build_contexts(g, prob, ks, prec, nl_engine=1):
     import torch
     ctxs = []
@@ -212,8 +269,19 @@ def run_gpu(args):
     M = prob.nnodes
     units_per_step = M * nvec * degree * len(ks)
 
+    # ---- arithmetic peaks of this GPU (the roofline denominators), measured by the
+    # library's probes before anything else runs
+    peaks = {}
+    for w in ("ffma", "ffma2", "dfma", "tf32", "bf16"):
+        try:
+            peaks[w] = round(g.alu_peak(w)[0] / 1e12, 2)
+        except Exception as exc:   # pragma: no cover - reported, not fatal
+            peaks[w] = f"{type(exc).__name__}: {exc}"
+
     # ---- contexts, blocks, bounds (outside the timed region)
     ctx32 = build_contexts(g, prob, ks, g.FP32, args.nl_engine)
+    for c in ctx32:
+        c.tune(nvec)             # FP32 cell-apply variant (cached per p, k, block size)
     X0 = syn.random_block(M, nvec, 0)
     v0 = torch.from_numpy(syn.random_start(M, 0)).cuda()
     bounds = []
@@ -277,23 +345,27 @@ def run_gpu(args):
     kpt = any(abs(x) > 0 for k in ks for x in k)
     flops_launch = flops_per_cell_vector(prob.p, prob.nq, kpt) * prob.ncells * nvec
     clocks = clk.summary()
-    peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
-    # DRAM bytes of one hx_local launch: ncu dram__bytes_read + write of the same kernel on the
-    # cube16_p6 mesh at 32 vectors (1.364 GB, of which 34 MB fields), scaled by the vector count
-    # (X gather and Y read-modify-write grow with it)
-    if args.config == "cube16_p6":
-        traffic = 0.034e9 + (1.364e9 - 0.034e9) * nvec / 32
-        traffic_note = "ncu capture at 32 vectors scaled by vectors; = algorithmic X read + Y RMW"
+    fp32 = [v for k, v in peaks.items() if k in ("ffma", "ffma2") and isinstance(v, float)]
+    if fp32:
+        peak_alu = max(fp32)
+        peak_note = ("of measured: FP32 FMA probe (gbc_alu_peak ffma / ffma2, best of three "
+                     "launches) on this GPU in this run")
     else:
-        traffic, traffic_note = None, "no capture for this configuration"
-
-    roofline = {"bound": "alu", "kernel": "hx_local_kernel<float,7,8,k!=0,2> (even-odd sum factorisation)",
+        peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12
+        peak_note = "derived (probe failed): 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+    var, vb, nt = ctx32[0].cell_variant()
+    traffic, traffic_note = None, "no ncu capture of this kernel version"
+    if args.config == "cube16_p6":
+        traffic, traffic_note = CELL_TRAFFIC(nvec)
+    roofline = {"bound": "alu",
+                "kernel": f"hx_cell_kernel<7,8,k!=0,VB={vb},NT={nt}> variant {var} (even-odd sum "
+                          "factorisation, recurrence fused for cell-interior nodes)",
                 "achieved": round(flops_launch / (avg_local_ms / 1e3) / 1e12, 3),
                 "peak": round(peak_alu, 2), "unit": "TFLOP/s",
                 "frac": round(flops_launch / (avg_local_ms / 1e3) / 1e12 / peak_alu, 4),
                 "traffic": traffic,
                 "traffic_note": traffic_note,
-                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",
+                "peak_note": peak_note,
                 "flops_per_launch": flops_launch}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -305,7 +377,7 @@ def run_gpu(args):
                       "parallelism": f"replicas x{world}",
                       "nonlocal_engine": ["simt", "tensor"][ctx32[0].nonlocal_engine()]},
            "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
-           "kernels": kernels}
+           "kernels": kernels, "peaks_measured_tflops": peaks}
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region):
     # each k-point block is uploaded on a copy stream, filtered on the compute stream once
@@ -383,6 +455,15 @@ def run_gpu(args):
             torch.cuda.synchronize()
             out["e2e"] = e2e_sequential()
             out["e2e"]["pipelined_error"] = f"{type(exc).__name__}: {exc}"
+
+    # ---- the cell apply on the tensor cores (precision paths TF32 and BF16x3): one H.X of
+    # the k-point-0 block per precision, the cell-apply family's CUDA-event time against the
+    # FP32 SIMT kernel's, dense products counted as computed (tensor work x3 for BF16x3)
+    if not args.no_tc and rank == 0:
+        try:
+            out["tc_cell"] = tc_cell_leg(g, prob, ks[0], X32[0], nvec, peaks, avg_local_ms)
+        except Exception as exc:   # an auxiliary leg must not cost the headline line
+            out["tc_cell"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     # ---- densities rho, m at the Gauss points from the filtered block (Eqs. rho, mag):
     # one gbc_density_dev launch on device-resident inputs, Fermi-Dirac occupations of the
@@ -890,6 +971,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-density", action="store_true")
     ap.add_argument("--no-twogrid", action="store_true")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core cell-apply leg")
     ap.add_argument("--scf-steps", type=int, default=2, help="SCF steps of the scf leg (0: off)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

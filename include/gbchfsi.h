@@ -339,14 +339,30 @@ gbc_status gbc_batch_launches(const gbc_batch* batch, int* kernels_per_call);
 
 /* ---- tile autotuner ------------------------------------------------------------ */
 
-/* Choose the FP32 cell-apply tile (1 or 2 vectors per CTA) for this context by
- * timing both on a scratch block of ``nvec`` vectors (CUDA events); the choice
- * is cached per (device, p, k != 0, nvec rounded up to a power of two) for the
- * process and, when the environment variable GBC_TUNE_CACHE names a file,
- * across processes.  Synchronous.  Uses the context's workspace. */
+/* Autotuner of the FP32 path: times every compiled cell-apply variant (vectors
+ * per CTA, threads per CTA, CTAs per SM the registers are sized for, paired or
+ * scalar FP32 arithmetic; see gbc_get_cell_variant) in the filter's recurrence
+ * mode, and, when the context has projectors the tensor-core engine takes, the
+ * SIMT and tcgen05 nonlocal engines, on a scratch block of ``nvec`` vectors (CUDA
+ * events, median of three after a warm-up), and keeps the fastest of each.  The
+ * choice is cached per (device, FP32, p, k != 0, nvec rounded up to a power of
+ * two) for the process and, when the environment variable GBC_TUNE_CACHE names a
+ * file, across processes in that JSON file (with the measured times).
+ * Synchronous.  Uses the context's workspace. */
 gbc_status gbc_tune(gbc_ctx* ctx, int nvec, void* stream);
 /* Vectors per CTA the cell apply of this context uses. */
 gbc_status gbc_get_tile(const gbc_ctx* ctx, int* vectors_per_cta);
+/* Set (overriding the tuner) / read the FP32 cell-apply variant, 0 ..
+ * GBC_CELL_VARIANTS - 1: 0 = 2 vectors x 256 threads with registers for 4 CTAs
+ * per SM, paired FP32 multiply-adds on (re, im); 1 = the same tile with
+ * registers for 3 CTAs per SM; 2 and 3 = variants 0 and 1 with scalar FP32
+ * multiply-adds.  gbc_get_cell_variant
+ * also returns the variant's vectors and threads per CTA (either pointer may be
+ * NULL).  GBC_EINVAL for a variant out of range. */
+#define GBC_CELL_VARIANTS 4
+gbc_status gbc_set_cell_variant(gbc_ctx* ctx, int variant);
+gbc_status gbc_get_cell_variant(const gbc_ctx* ctx, int* variant, int* vectors_per_cta,
+                                int* threads_per_cta);
 
 /* ---- allocation-free variant ------------------------------------------------ */
 
@@ -367,7 +383,8 @@ gbc_status gbc_get_tile(const gbc_ctx* ctx, int* vectors_per_cta);
  * on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the array
  * and it keeps the previous call's contents; calls that overlap on the GPU
- * race on it, so callers must order them. */
+ * race on it, so callers must order them.  X or Y null, equal, or not device
+ * (or managed) memory: GBC_EINVAL. */
 gbc_status gbc_apply_h_noalloc(gbc_ctx* ctx, const void* X, void* Y, int nvec, int ldx,
                                void* stream);
 
@@ -409,6 +426,26 @@ gbc_status gbc_set_timing(gbc_ctx* ctx, int enable);
 /* Total device time (ms, summed over launches) and launch count of ``family``
  * since the last gbc_set_timing.  Waits for the recorded events. */
 gbc_status gbc_get_timing(gbc_ctx* ctx, int family, double* total_ms, long long* launches);
+
+/* ---- arithmetic peaks (the roofline denominators) ------------------------- */
+
+/* Probes of the current device's arithmetic throughput, so that each kernel's
+ * achieved rate is reported as a fraction of a measured peak (the paper states
+ * none; this is measurement plumbing).  ``which``: */
+enum {
+  GBC_PEAK_FFMA = 0,      /* FP32 FMA, one per instruction                 */
+  GBC_PEAK_FFMA2 = 1,     /* FP32 paired FMA (two per instruction)         */
+  GBC_PEAK_DFMA = 2,      /* FP64 FMA                                      */
+  GBC_PEAK_TF32 = 3,      /* tcgen05.mma kind::tf32, 128 x 256 x 8         */
+  GBC_PEAK_BF16 = 4       /* tcgen05.mma kind::f16 (BF16), 128 x 256 x 16  */
+};
+/* Runs one probe (a warm-up launch, then the best of three timed with CUDA
+ * events on ``stream``) on the current device and returns its rate in FLOP/s
+ * (2 per multiply-add) and the timed launch's duration in seconds (``seconds``
+ * may be NULL).  Synchronous; allocates nothing.  GBC_EINVAL for an unknown
+ * probe or a null rate pointer, GBC_ETIMEOUT if a tensor-core probe's bounded
+ * completion wait expired. */
+gbc_status gbc_alu_peak(int which, double* flops_per_s, double* seconds, void* stream);
 
 #ifdef __cplusplus
 }

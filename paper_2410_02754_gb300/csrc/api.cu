@@ -25,6 +25,17 @@ gbc_status gbc_cuda_fail(gbc_ctx* c, cudaError_t e, const char* where) {
   return gbc_fail(c, e == cudaErrorMemoryAllocation ? GBC_ENOMEM : GBC_ECUDA, m);
 }
 
+int gbc_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < 64 && cache[dev] > 0) return cache[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  if (dev < 64) cache[dev] = n;
+  return n;
+}
+
 bool gbc_is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a{};
@@ -116,10 +127,14 @@ gbc_status apply_h_t(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx
   cudaError_t e;
   {
     TimerScope ts(c, FAM_HX_LOCAL, s);
-    if (std::is_same<T, double>::value)
+    if (std::is_same<T, double>::value) {
       e = launch_hx_local_f64(c, (const double2*)X, (double2*)Y, nvec, ldx, s);
-    else
+    } else if (c->prec == GBC_TF32 || c->prec == GBC_BF16X3) {
+      GBC_TRY(tcl_apply(c, (const float2*)X, (float2*)Y, nvec, ldx, c->prec == GBC_BF16X3 ? 1 : 0, s));
+      e = cudaSuccess;
+    } else {
       e = launch_hx_local_f32(c, (const float2*)X, (float2*)Y, nvec, ldx, s);
+    }
   }
   if (e != cudaSuccess) return gbc_cuda_fail(c, e, "hx_local");
   if (c->proj.natoms > 0) {
@@ -136,6 +151,12 @@ gbc_status apply_h_t(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx
   return GBC_OK;
 }
 
+// X <- p_m(H~) X in place, the sigma-scaled three-term recurrence of Eq. chebfilt.
+// FP64: the H.X accumulation (cell apply, nonlocal step) then one recurrence
+// pass over every row.  FP32: the recurrence is fused into the applies -- the
+// nonlocal step writes P C' into the accumulator's support rows, the cell apply
+// finishes the rows interior to a cell in its epilogue, and a row pass finishes
+// the rows on cell faces (see hx_cell.cuh).
 template <typename T>
 gbc_status filter_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, int m, double lT, double lmax,
                     double lmin, cudaStream_t s) {
@@ -150,20 +171,36 @@ gbc_status filter_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, int m, double lT,
   cplx<T>* W = (cplx<T>*)c->work[1];
   const T* invmd = std::is_same<T, double>::value ? (const T*)c->d_invmd : (const T*)c->d_invmd32;
   GBC_CU(c, cudaMemsetAsync(Y, 0, bytes, s));
-  // X_1 = (sigma_1/e)(H~ - c) X_0  -> W
-  GBC_TRY(apply_h_t<T>(c, X, Y, nvec, ldx, s, false));
-  {
+  // step k: X_{k+1} = a_k (M_D^-1 H X_k - c X_k) - b_k X_{k-1}; X_1 -> W, then
+  // X_{k+1} written over X_{k-1}
+  for (int k = 0; k < m; ++k) {
+    cplx<T>* cur = k == 0 ? X : ((k & 1) ? W : X);
+    cplx<T>* prev = k == 0 ? nullptr : ((k & 1) ? X : W);
+    cplx<T>* out = k == 0 ? W : prev;
+    const double a = k == 0 ? sig[0] / e : 2.0 * sig[k] / e;
+    const double b = k == 0 ? 0.0 : sig[k - 1] * sig[k];
+    if (std::is_same<T, double>::value || nvec == 0 || c->prec != GBC_FP32) {
+      GBC_TRY(apply_h_t<T>(c, cur, Y, nvec, ldx, s, false));
+      TimerScope ts(c, FAM_CHEB, s);
+      GBC_CU(c, launch_cheb_step<T>(Y, cur, prev, out, invmd, c->mesh.M, nvec, ldx, a, cc, b, s));
+      continue;
+    }
+    if (c->proj.natoms > 0) {
+      const size_t cb = sizeof(cplx<T>) * (size_t)c->proj.rows_total * nvec;
+      GBC_TRY(gbc_ensure_work(c, 2, 2 * cb));
+      cplx<T>* C1 = (cplx<T>*)c->work[2];
+      cplx<T>* C2 = C1 + (size_t)c->proj.rows_total * nvec;
+      TimerScope ts(c, FAM_NONLOCAL, s);
+      GBC_CU(c, launch_nonlocal<T>(c, cur, Y, nvec, ldx, C1, C2, s, true));
+    }
+    {
+      TimerScope ts(c, FAM_HX_LOCAL, s);
+      CellJob j{c, cur, Y, nvec, ldx, out, prev, a, cc, b};
+      GBC_CU(c, launch_cell_f32(&j, 1, c->cell_var, s));
+    }
     TimerScope ts(c, FAM_CHEB, s);
-    GBC_CU(c, launch_cheb_step<T>(Y, X, nullptr, W, invmd, c->mesh.M, nvec, ldx, sig[0] / e, cc, 0.0, s));
-  }
-  // X_{k+1} = (2 sigma_{k+1}/e)(H~ - c) X_k - sigma_k sigma_{k+1} X_{k-1}, written over X_{k-1}
-  for (int k = 1; k < m; ++k) {
-    cplx<T>* cur = (k & 1) ? W : X;
-    cplx<T>* prev = (k & 1) ? X : W;
-    GBC_TRY(apply_h_t<T>(c, cur, Y, nvec, ldx, s, false));
-    TimerScope ts(c, FAM_CHEB, s);
-    GBC_CU(c, launch_cheb_step<T>(Y, cur, prev, prev, invmd, c->mesh.M, nvec, ldx,
-                                  2.0 * sig[k] / e, cc, sig[k - 1] * sig[k], s));
+    GBC_CU(c, launch_cheb_rows<T>(Y, cur, prev, out, invmd, c->d_face_rows, c->nface, nvec, ldx,
+                                  a, cc, b, s));
   }
   if (m & 1) GBC_CU(c, launch_copy_block<T>(W, X, c->mesh.M, nvec, ldx, s));
   return GBC_OK;
@@ -412,6 +449,7 @@ void gbc_destroy(gbc_ctx* c) {
   cudaSetDevice(c->dev);
   cudaDeviceSynchronize();
   free_projectors(c->proj);
+  tcl_free(c->tcl);
   for (auto& t : c->timed) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
@@ -419,7 +457,8 @@ void gbc_destroy(gbc_ctx* c) {
   for (auto e : c->event_pool) cudaEventDestroy(e);
   void* ptrs[] = {c->d_md, c->d_invmd, c->d_invmd32, c->d_rawfields, c->d_fields64, c->d_fields32,
                   c->work[0], c->work[1], c->work[2], c->work[3], c->work[4], c->work[5],
-                  c->work[6], c->work[7], c->work[8], c->work[9], c->d_small, c->d_flag};
+                  c->work[6], c->work[7], c->work[8], c->work[9], c->d_small, c->d_flag,
+                  c->d_face_rows};
   for (void* p : ptrs) cudaFree(p);
   delete c;
 }
@@ -467,6 +506,7 @@ gbc_status gbc_set_mesh(gbc_ctx* c, const int ncell[3], const double h[3], int p
   c->proj_dirty = false;
   GBC_TRY(setup_tables(c));
   GBC_TRY(setup_mass(c));
+  GBC_TRY(setup_face_rows(c));
   c->mesh_set = true;
   return GBC_OK;
 }
@@ -524,9 +564,8 @@ gbc_status gbc_set_projectors(gbc_ctx* c, int natoms, const int* npj, const int*
 
 gbc_status gbc_set_precision(gbc_ctx* c, gbc_precision prec) {
   if (!c) return GBC_EINVAL;
-  if (prec == GBC_TF32 || prec == GBC_BF16X3)
-    return gbc_fail(c, GBC_EUNSUPPORTED, "tensor-core cell apply precisions are not built");
-  if (prec != GBC_FP64 && prec != GBC_FP32) return gbc_fail(c, GBC_EUNSUPPORTED, "unknown precision");
+  if (prec != GBC_FP64 && prec != GBC_FP32 && prec != GBC_TF32 && prec != GBC_BF16X3)
+    return gbc_fail(c, GBC_EUNSUPPORTED, "unknown precision");
   c->prec = prec;
   return GBC_OK;
 }
@@ -551,6 +590,9 @@ gbc_status gbc_sync_status(gbc_ctx* c, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   int err = 0;
   GBC_CU(c, tc_nonlocal_error(&err, s));
+  int err2 = 0;
+  GBC_CU(c, tcl_error(&err2, s));
+  err |= err2;
   if (err) {
     GBC_CU(c, tc_nonlocal_reset(s));
     GBC_CU(c, cudaStreamSynchronize(s));

@@ -32,17 +32,25 @@ cudaError_t launch_hx_local_f64(const gbc_ctx* c, const double2* X, double2* Y, 
 
 cudaError_t launch_hx_local_f32(const gbc_ctx* c, const float2* X, float2* Y, int nvec, int ldx,
                                 cudaStream_t s) {
-  HxJob j{c, X, Y, nvec, ldx};
-  return launch_hx_local_group_f32(&j, 1, c->vb32, s);
+  CellJob j{c, X, Y, nvec, ldx, nullptr, nullptr, 0.0, 0.0, 0.0};
+  return launch_cell_f32(&j, 1, c->cell_var, s);
 }
 
 // ---------------------------------------------------------------------------
-// autotuner: vectors per CTA of the FP32 cell apply
+// autotuner: variant (vectors per CTA, threads, CTAs per SM) of the FP32 cell apply
 // ---------------------------------------------------------------------------
 namespace {
 
+// one tuned configuration: the cell-apply variant and the FP32 nonlocal engine, with
+// the times that chose them
+struct TuneEntry {
+  int variant = 0, nl_engine = -1;   // nl_engine -1: not tuned (no atoms)
+  float ms[GBC_CELL_VARIANTS] = {0, 0, 0, 0};
+  float nl_ms[2] = {0, 0};
+};
+
 std::mutex g_tune_mu;
-std::map<std::string, int> g_tune_cache;   // key -> vb
+std::map<std::string, TuneEntry> g_tune_cache;
 bool g_tune_loaded = false;
 
 std::string tune_file() {
@@ -50,7 +58,8 @@ std::string tune_file() {
   return f ? std::string(f) : std::string();
 }
 
-// cache file: one "key vb" pair per line
+// JSON cache, one entry per line:
+//   "key": {"variant": v, "nl_engine": e, "ms": [..], "nl_ms": [..]},
 void tune_load() {
   if (g_tune_loaded) return;
   g_tune_loaded = true;
@@ -58,9 +67,15 @@ void tune_load() {
   if (f.empty()) return;
   FILE* fp = std::fopen(f.c_str(), "r");
   if (!fp) return;
-  char key[512];
-  int vb = 0;
-  while (std::fscanf(fp, "%511s %d", key, &vb) == 2) g_tune_cache[key] = vb;
+  char line[1024];
+  while (std::fgets(line, sizeof line, fp)) {
+    char key[512];
+    TuneEntry e;
+    if (std::sscanf(line, " \"%511[^\"]\": {\"variant\": %d, \"nl_engine\": %d", key, &e.variant,
+                    &e.nl_engine) == 3 &&
+        e.variant >= 0 && e.variant < GBC_CELL_VARIANTS)
+      g_tune_cache[key] = e;
+  }
   std::fclose(fp);
 }
 
@@ -69,10 +84,21 @@ void tune_store() {
   if (f.empty()) return;
   FILE* fp = std::fopen(f.c_str(), "w");
   if (!fp) return;
-  for (auto& kv : g_tune_cache) std::fprintf(fp, "%s %d\n", kv.first.c_str(), kv.second);
+  std::fprintf(fp, "{\n");
+  size_t i = 0;
+  for (auto& kv : g_tune_cache) {
+    const TuneEntry& e = kv.second;
+    std::fprintf(fp, "  \"%s\": {\"variant\": %d, \"nl_engine\": %d, \"ms\": [", kv.first.c_str(),
+                 e.variant, e.nl_engine);
+    for (int v = 0; v < GBC_CELL_VARIANTS; ++v) std::fprintf(fp, "%s%.4f", v ? ", " : "", e.ms[v]);
+    std::fprintf(fp, "], \"nl_ms\": [%.4f, %.4f]}%s\n", e.nl_ms[0], e.nl_ms[1],
+                 ++i < g_tune_cache.size() ? "," : "");
+  }
+  std::fprintf(fp, "}\n");
   std::fclose(fp);
 }
 
+// key: device, precision, order p, k != 0, vectors (rounded up to a power of two)
 std::string tune_key(const gbc_ctx* c, int nvec) {
   cudaDeviceProp prop;
   std::string dev = "gpu";
@@ -88,6 +114,23 @@ std::string tune_key(const gbc_ctx* c, int nvec) {
   return buf;
 }
 
+// median of three timed launches after a warm-up (ms); negative if a launch failed
+template <typename F>
+float time_median(gbc_ctx* c, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, F launch) {
+  float t[4];
+  for (int rep = 0; rep < 4; ++rep) {
+    if (cudaEventRecord(e0, s) != cudaSuccess) return -1.f;
+    if (launch() != cudaSuccess) {
+      cudaGetLastError();
+      return -1.f;
+    }
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+    cudaEventElapsedTime(&t[rep], e0, e1);
+  }
+  std::sort(t + 1, t + 4);   // t[0] is the warm-up
+  return t[2];
+}
+
 }  // namespace
 
 extern "C" gbc_status gbc_tune(gbc_ctx* c, int nvec, void* stream) {
@@ -100,10 +143,11 @@ extern "C" gbc_status gbc_tune(gbc_ctx* c, int nvec, void* stream) {
   const std::string key = tune_key(c, nvec);
   auto it = g_tune_cache.find(key);
   if (it != g_tune_cache.end()) {
-    c->vb32 = it->second;
+    c->cell_var = it->second.variant;
+    if (it->second.nl_engine >= 0) c->nl_engine = it->second.nl_engine;
     return GBC_OK;
   }
-  // time each candidate tile on a scratch block (work slots 0 and 1)
+  // every candidate timed on a scratch block (work slots 0, 1, 2)
   const size_t bytes = sizeof(float2) * 2 * (size_t)c->mesh.M * nvec;
   GBC_TRY(gbc_ensure_work(c, 0, bytes));
   GBC_TRY(gbc_ensure_work(c, 1, bytes));
@@ -113,38 +157,79 @@ extern "C" gbc_status gbc_tune(gbc_ctx* c, int nvec, void* stream) {
   cudaEvent_t e0, e1;
   GBC_CU(c, cudaEventCreate(&e0));
   GBC_CU(c, cudaEventCreate(&e1));
-  const int cands[2] = {1, 2};
+  TuneEntry ent;
   float best = 1e30f;
-  int best_vb = 2;
-  for (int vb : cands) {
-    HxJob j{c, X, Y, nvec, nvec};
-    float tot = 0;
-    for (int rep = 0; rep < 3; ++rep) {
-      GBC_CU(c, cudaEventRecord(e0, s));
-      GBC_CU(c, launch_hx_local_group_f32(&j, 1, vb, s));
-      GBC_CU(c, cudaEventRecord(e1, s));
-      GBC_CU(c, cudaEventSynchronize(e1));
-      float ms = 0;
-      GBC_CU(c, cudaEventElapsedTime(&ms, e0, e1));
-      if (rep > 0) tot += ms;   // first launch is a warm-up
+  for (int var = 0; var < GBC_CELL_VARIANTS; ++var) {
+    // timed in the filter's recurrence mode (the scratch block is zero, so writing
+    // the update over it changes nothing); a variant whose shared memory does not
+    // fit this order is skipped
+    CellJob j{c, X, Y, nvec, nvec, X, X, 0.0, 0.0, 0.0};
+    const float ms = time_median(c, s, e0, e1, [&] { return launch_cell_f32(&j, 1, var, s); });
+    ent.ms[var] = ms;
+    if (ms >= 0.f && ms < best) {
+      best = ms;
+      ent.variant = var;
     }
-    if (tot < best) {
-      best = tot;
-      best_vb = vb;
+  }
+  // FP32 nonlocal engine: the SIMT kernels against the tcgen05 contractions
+  if (c->proj.natoms > 0 && tc_nonlocal_supported(c->proj)) {
+    const size_t cb = sizeof(float2) * (size_t)c->proj.rows_total * nvec;
+    GBC_TRY(gbc_ensure_work(c, 2, 2 * cb));
+    float2* C1 = (float2*)c->work[2];
+    float2* C2 = C1 + (size_t)c->proj.rows_total * nvec;
+    const int keep = c->nl_engine;
+    float nlbest = 1e30f;
+    for (int eng = 0; eng < 2; ++eng) {
+      c->nl_engine = eng;
+      const float ms = time_median(c, s, e0, e1, [&] {
+        return launch_nonlocal<float>(c, X, Y, nvec, nvec, C1, C2, s, true);
+      });
+      ent.nl_ms[eng] = ms;
+      if (ms >= 0.f && ms < nlbest) {
+        nlbest = ms;
+        ent.nl_engine = eng;
+      }
+    }
+    c->nl_engine = ent.nl_engine >= 0 ? ent.nl_engine : keep;
+    int err = 0;
+    GBC_CU(c, tc_nonlocal_error(&err, s));
+    if (err) {
+      GBC_CU(c, tc_nonlocal_reset(s));
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return gbc_fail(c, GBC_ETIMEOUT, "a tensor-core wait expired while tuning");
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   GBC_CU(c, cudaMemsetAsync(Y, 0, bytes, s));
-  c->vb32 = best_vb;
-  g_tune_cache[key] = best_vb;
+  c->cell_var = ent.variant;
+  g_tune_cache[key] = ent;
   tune_store();
+  return GBC_OK;
+}
+
+extern "C" gbc_status gbc_set_cell_variant(gbc_ctx* c, int variant) {
+  if (!c) return GBC_EINVAL;
+  if (variant < 0 || variant >= GBC_CELL_VARIANTS)
+    return gbc_fail(c, GBC_EINVAL, "cell-apply variant out of range");
+  c->cell_var = variant;
+  return GBC_OK;
+}
+
+extern "C" gbc_status gbc_get_cell_variant(const gbc_ctx* c, int* variant, int* vectors_per_cta,
+                                           int* threads_per_cta) {
+  if (!c || !variant) return GBC_EINVAL;
+  *variant = c->cell_var;
+  const CellVariant v = cell_variant(c->cell_var);
+  if (vectors_per_cta) *vectors_per_cta = v.vb;
+  if (threads_per_cta) *threads_per_cta = v.nt;
   return GBC_OK;
 }
 
 extern "C" gbc_status gbc_get_tile(const gbc_ctx* c, int* vectors_per_cta) {
   if (!c || !vectors_per_cta) return GBC_EINVAL;
-  *vectors_per_cta = c->prec == GBC_FP64 ? 1 : c->vb32;
+  *vectors_per_cta = c->prec == GBC_FP64 ? 1 : cell_variant(c->cell_var).vb;
   return GBC_OK;
 }
 
@@ -210,7 +295,81 @@ gbc_status record_filters(gbc_batch* b, std::vector<SysRun>& runs, cudaStream_t 
     for (int i = 0; i < (int)runs.size(); ++i)
       if (runs[i].degree > k) active.push_back(i);
     auto cur_of = [&](const SysRun& r) { return k == 0 ? r.X : ((k & 1) ? r.W : r.X); };
-    // cell-level applies: one launch per group of systems sharing the tables and tile
+    if constexpr (std::is_same<T, float>::value) {
+      // fused recurrence: nonlocal terms written into the accumulators, cell applies
+      // finishing the cell-interior rows, row passes finishing the cell-face rows
+      for (int i : active) {
+        SysRun& r = runs[i];
+        if (r.c->proj.natoms == 0) continue;
+        float2* C1 = (float2*)r.c->work[2];
+        float2* C2 = C1 + (size_t)r.c->proj.rows_total * r.nvec;
+        const cudaError_t e = launch_nonlocal<float>(r.c, (const float2*)cur_of(r), (float2*)r.Y,
+                                                     r.nvec, r.ldx, C1, C2, s, true);
+        if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("nonlocal: ") + cudaGetErrorString(e));
+        count += 3;
+      }
+      auto step = [&](const SysRun& r, void** cur, void** prev, void** out, double* a, double* bb) {
+        *cur = cur_of(r);
+        *prev = k == 0 ? nullptr : ((k & 1) ? r.X : r.W);
+        *out = k == 0 ? r.W : *prev;
+        *a = k == 0 ? r.sig[0] / r.e : 2.0 * r.sig[k] / r.e;
+        *bb = k == 0 ? 0.0 : r.sig[k - 1] * r.sig[k];
+      };
+      // the cell applies of every active system, whatever its order, in one
+      // persistent launch (per-order groups of CTAs); per-table-group launches only
+      // when systems of one order differ in cell edges or k-point
+      std::vector<CellJob> all;
+      for (int i : active) {
+        void *cur, *prev, *out;
+        double a, bb;
+        step(runs[i], &cur, &prev, &out, &a, &bb);
+        all.push_back(CellJob{runs[i].c, cur, runs[i].Y, runs[i].nvec, runs[i].ldx, out, prev, a,
+                              runs[i].cc, bb});
+      }
+      cudaError_t em = cudaErrorInvalidValue;
+      if ((int)all.size() <= GBC_MAX_SYS) em = launch_cell_multi_f32(all.data(), (int)all.size(), s);
+      if (em == cudaSuccess) {
+        ++count;
+      } else if (em != cudaErrorInvalidValue) {
+        return bfail(b, GBC_ECUDA, std::string("cell apply: ") + cudaGetErrorString(em));
+      } else {
+        std::vector<bool> done(all.size(), false);
+        for (size_t i = 0; i < all.size(); ++i) {
+          if (done[i]) continue;
+          std::vector<CellJob> jobs;
+          for (size_t j = i; j < all.size() && (int)jobs.size() < GBC_MAX_SYS; ++j) {
+            if (done[j] || !same_tables(all[i].c, all[j].c) || all[i].c->cell_var != all[j].c->cell_var)
+              continue;
+            jobs.push_back(all[j]);
+            done[j] = true;
+          }
+          const cudaError_t e = launch_cell_f32(jobs.data(), (int)jobs.size(), all[i].c->cell_var, s);
+          if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("cell apply: ") + cudaGetErrorString(e));
+          ++count;
+        }
+      }
+      // cell-face rows of every active system, one launch
+      for (size_t a0 = 0; a0 < active.size(); a0 += GBC_MAX_CHEB_BATCH) {
+        ChebRowsBatch cb;
+        cb.njobs = 0;
+        cb.total = 0;
+        for (size_t ai = a0; ai < active.size() && cb.njobs < GBC_MAX_CHEB_BATCH; ++ai) {
+          SysRun& r = runs[active[ai]];
+          void *cur, *prev, *out;
+          double a, bb;
+          step(r, &cur, &prev, &out, &a, &bb);
+          ChebRowsJob& j = cb.job[cb.njobs++];
+          j = ChebRowsJob{r.Y, cur, prev, out, r.c->d_invmd32, r.c->d_face_rows, cb.total,
+                          r.nvec, r.ldx, a, r.cc, bb};
+          cb.total += r.c->nface * 2LL * r.nvec;
+        }
+        const cudaError_t e = launch_cheb_rows_batch<float>(cb, s);
+        if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("recurrence: ") + cudaGetErrorString(e));
+        ++count;
+      }
+      continue;
+    }
+    // cell-level applies: one launch per group of systems sharing the tables
     std::vector<bool> done(runs.size(), false);
     for (size_t ai = 0; ai < active.size(); ++ai) {
       const int i = active[ai];
@@ -218,15 +377,11 @@ gbc_status record_filters(gbc_batch* b, std::vector<SysRun>& runs, cudaStream_t 
       std::vector<HxJob> jobs;
       for (size_t aj = ai; aj < active.size() && (int)jobs.size() < GBC_MAX_BATCH; ++aj) {
         const int j = active[aj];
-        if (done[j] || !same_tables(runs[i].c, runs[j].c) || runs[i].c->vb32 != runs[j].c->vb32)
-          continue;
+        if (done[j] || !same_tables(runs[i].c, runs[j].c)) continue;
         jobs.push_back(HxJob{runs[j].c, cur_of(runs[j]), runs[j].Y, runs[j].nvec, runs[j].ldx});
         done[j] = true;
       }
-      const cudaError_t e = std::is_same<T, double>::value
-                                ? launch_hx_local_group_f64(jobs.data(), (int)jobs.size(), 1, s)
-                                : launch_hx_local_group_f32(jobs.data(), (int)jobs.size(),
-                                                            runs[i].c->vb32, s);
+      const cudaError_t e = launch_hx_local_group_f64(jobs.data(), (int)jobs.size(), 1, s);
       if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("cell apply: ") + cudaGetErrorString(e));
       ++count;
     }
@@ -300,6 +455,7 @@ gbc_status gbc_batch_create(gbc_batch** out, int nsys, gbc_ctx* const* systems) 
   if (nsys < 1 || nsys > 256 || !systems) return GBC_EINVAL;
   for (int i = 0; i < nsys; ++i) {
     if (!systems[i] || !systems[i]->mesh_set) return GBC_ESTATE;
+    if (systems[i]->prec == GBC_TF32 || systems[i]->prec == GBC_BF16X3) return GBC_EUNSUPPORTED;
     if (systems[i]->dev != systems[0]->dev || systems[i]->prec != systems[0]->prec)
       return GBC_EINVAL;
     for (int j = 0; j < i; ++j)
@@ -361,7 +517,7 @@ gbc_status gbc_batch_filter(gbc_batch* b, void* const* X, const int* nvec, const
     r.sig[0] = r.e / (lmin - r.cc);
     for (int k = 1; k < degree[i]; ++k) r.sig[k] = 1.0 / (2.0 / r.sig[0] - r.sig[k - 1]);
     key.insert(key.end(), {(double)(uintptr_t)X[i], (double)nvec[i], (double)ldx[i],
-                           (double)degree[i], lT, lmax, lmin, (double)c->vb32,
+                           (double)degree[i], lT, lmax, lmin, (double)c->cell_var,
                            (double)(uintptr_t)c->work[0], (double)(uintptr_t)c->work[1],
                            (double)(uintptr_t)c->work[2]});
   }

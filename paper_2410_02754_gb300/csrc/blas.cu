@@ -461,12 +461,101 @@ __global__ void k_divmass(double2* y, const double* __restrict__ invmd, long lon
 
 inline unsigned grid_for(long long n, int threads = 256) {
   long long g = (n + threads - 1) / threads;
-  if (g > 152LL * 64) g = 152LL * 64;
+  const long long cap = 64LL * gbc_sm_count();
+  if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (unsigned)g;
 }
 
 }  // namespace
+
+// Recurrence update on the listed node rows only (the rows the fused cell
+// apply leaves to atomics: nodes on cell faces), Y zeroed there for the next step.
+template <typename T>
+__global__ void k_cheb_rows(cplx<T>* __restrict__ Y, const cplx<T>* Xcur, const cplx<T>* Xprev,
+                            cplx<T>* Xout, const T* __restrict__ invmd,
+                            const long long* __restrict__ rows, long long nrows, int nvec, int ldx,
+                            T a, T cshift, T b) {
+  const long long n = nrows * 2 * (long long)nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long rs = i / nvec;
+    const int v = (int)(i - rs * nvec);
+    const long long node = rows[rs >> 1];
+    const long long o = (node * 2 + (rs & 1)) * ldx + v;
+    const T w = invmd[node];
+    const cplx<T> y = Y[o];
+    const cplx<T> x = Xcur[o];
+    cplx<T> out;
+    out.x = a * (w * y.x - cshift * x.x);
+    out.y = a * (w * y.y - cshift * x.y);
+    if (Xprev) {
+      const cplx<T> xp = Xprev[o];
+      out.x -= b * xp.x;
+      out.y -= b * xp.y;
+    }
+    Xout[o] = out;
+    Y[o] = cmake<cplx<T>>(0, 0);
+  }
+}
+
+template <typename T>
+cudaError_t launch_cheb_rows(cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev, cplx<T>* Xout,
+                             const T* invmd, const long long* rows, long long nrows, int nvec,
+                             int ldx, double a, double cshift, double b, cudaStream_t s) {
+  if (nrows <= 0 || nvec <= 0) return cudaSuccess;
+  k_cheb_rows<T><<<grid_for(nrows * 2 * nvec), 256, 0, s>>>(Y, Xcur, Xprev, Xout, invmd, rows,
+                                                            nrows, nvec, ldx, (T)a, (T)cshift,
+                                                            (T)b);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cheb_rows<float>(float2*, const float2*, const float2*, float2*,
+                                             const float*, const long long*, long long, int, int,
+                                             double, double, double, cudaStream_t);
+template cudaError_t launch_cheb_rows<double>(double2*, const double2*, const double2*, double2*,
+                                              const double*, const long long*, long long, int,
+                                              int, double, double, double, cudaStream_t);
+
+// launch_cheb_rows over several systems in one launch (batched filter)
+template <typename T>
+__global__ void k_cheb_rows_batch(const __grid_constant__ ChebRowsBatch b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < b.total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int q = 0;
+    for (int r = 1; r < b.njobs; ++r)
+      if (i >= b.job[r].start) q = r;
+    const ChebRowsJob& j = b.job[q];
+    const long long li = i - j.start;
+    const long long rs = li / j.nvec;
+    const int v = (int)(li - rs * j.nvec);
+    const long long node = j.rows[rs >> 1];
+    const long long o = (node * 2 + (rs & 1)) * j.ldx + v;
+    cplx<T>* Y = (cplx<T>*)j.Y;
+    const cplx<T> y = Y[o];
+    const cplx<T> x = ((const cplx<T>*)j.Xcur)[o];
+    const T w = ((const T*)j.invmd)[node];
+    const T a = (T)j.a, c = (T)j.c, bb = (T)j.b;
+    cplx<T> out;
+    out.x = a * (w * y.x - c * x.x);
+    out.y = a * (w * y.y - c * x.y);
+    if (j.Xprev) {
+      const cplx<T> xp = ((const cplx<T>*)j.Xprev)[o];
+      out.x -= bb * xp.x;
+      out.y -= bb * xp.y;
+    }
+    ((cplx<T>*)j.Xout)[o] = out;
+    Y[o] = cmake<cplx<T>>(0, 0);
+  }
+}
+
+template <typename T>
+cudaError_t launch_cheb_rows_batch(const ChebRowsBatch& b, cudaStream_t s) {
+  if (b.total <= 0) return cudaSuccess;
+  k_cheb_rows_batch<T><<<grid_for(b.total), 256, 0, s>>>(b);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cheb_rows_batch<float>(const ChebRowsBatch&, cudaStream_t);
+template cudaError_t launch_cheb_rows_batch<double>(const ChebRowsBatch&, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_cheb_step(const cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev,
@@ -497,7 +586,7 @@ cudaError_t launch_gram(const cplx<T>* X, const cplx<T>* Y, const double* md, lo
   const int ntile = (nvec + GT - 1) / GT;
   const long long tiles = (long long)ntile * (ntile + 1) / 2;   // upper-triangle tiles
   // enough row chunks to fill the GPU a few times over
-  long long nchunk = (152LL * 8 + tiles - 1) / tiles;
+  long long nchunk = (8LL * gbc_sm_count() + tiles - 1) / tiles;
   long long per = (rows + nchunk - 1) / nchunk;
   per = ((per + GT - 1) / GT) * GT;
   if (per < GT) per = GT;
@@ -622,7 +711,7 @@ cudaError_t launch_gram_ff(const float2* X, int ldx, const cplx<TY>* Y, int ldy,
   if (e != cudaSuccess) return e;
   const int ntile = (nvec + GT - 1) / GT;
   const long long tiles = (long long)ntile * (ntile + 1) / 2;   // upper-triangle tiles
-  long long nchunk = (152LL * 8 + tiles - 1) / tiles;
+  long long nchunk = (8LL * gbc_sm_count() + tiles - 1) / tiles;
   long long per = (rows + nchunk - 1) / nchunk;
   per = ((per + GT - 1) / GT) * GT;
   if (per < GT) per = GT;

@@ -11,7 +11,8 @@
 
 #define GBC_MAX_P 7
 #define GBC_MAX_NPJ 32
-#define GBC_MAX_BATCH 8     // systems per cell-apply launch
+#define GBC_MAX_BATCH 8     // systems per FP64 cell-apply launch
+#define GBC_MAX_SYS 16      // systems per FP32 cell-apply launch
 #define GBC_TC_MAX_SLOTS 16 // atoms per tensor-core expansion chunk
 
 // ---------------------------------------------------------------------------
@@ -123,6 +124,8 @@ struct ProjDev {
   int rows_total = 0;                // sum 2*npj
 };
 
+struct TclState;   // tensor-core cell apply: dense operators and scratch (tc_cell.cu)
+
 struct gbc_ctx {
   int dev = 0;
   std::string err;
@@ -152,8 +155,12 @@ struct gbc_ctx {
   void* d_small = nullptr;           // small dense scratch (Gram, eigensolver)
   size_t small_bytes = 0;
   int* d_flag = nullptr;
-  int vb32 = 2;                      // FP32 cell-apply tile (vectors per CTA), set by the tuner
+  int vb32 = 2;                      // FP64 kernel tile (vectors per CTA; fixed)
+  int cell_var = 0;                  // FP32 cell-apply variant (GBC_CELL_VARIANTS), set by the tuner
+  long long nface = 0;               // free nodes on cell faces (shared by several cells)
+  long long* d_face_rows = nullptr;  // [nface] their node indices, ascending
   int nl_engine = 1;                 // FP32 projector contractions: 0 SIMT, 1 tensor cores
+  TclState* tcl = nullptr;           // GBC_TF32 / GBC_BF16X3 cell apply (built on first use)
   // optional per-kernel-family timing (gbc_set_timing)
   bool timing = false;
   struct TimedLaunch { int family; cudaEvent_t a, b; };
@@ -187,6 +194,8 @@ gbc_status gbc_cuda_fail(gbc_ctx* c, cudaError_t e, const char* where);
     if (_s != GBC_OK) return _s;          \
   } while (0)
 
+// streaming multiprocessors of the current device (queried once per device)
+int gbc_sm_count();
 gbc_status gbc_ensure_work(gbc_ctx* c, int slot, size_t bytes);
 gbc_status gbc_ensure_small(gbc_ctx* c, size_t bytes);
 gbc_status gbc_prepare(gbc_ctx* c);    // (re)builds fields / projector tables if dirty
@@ -208,24 +217,49 @@ struct HxJob {
   int nvec, ldx;
 };
 cudaError_t launch_hx_local_group_f64(const HxJob* jobs, int n, int vb, cudaStream_t s);
-cudaError_t launch_hx_local_group_f32(const HxJob* jobs, int n, int vb, cudaStream_t s);
-cudaError_t launch_hx_local_group_f32_vb1(const HxJob* jobs, int n, cudaStream_t s);
-cudaError_t launch_hx_local_group_f32_vb2(const HxJob* jobs, int n, cudaStream_t s);
+// hx_cell_*.cu : FP32 cell apply (paired FP32 arithmetic).  Accumulate mode
+// (Xout == null): Y += H^loc X.  Recurrence mode: nodes interior to a cell get
+// X_out = a (M_D^-1 (Y + (H^loc X)_row) - cshift X) - b X_prev directly, face
+// nodes are accumulated into Y for launch_cheb_rows.
+struct CellJob {
+  const gbc_ctx* c;
+  const void* X;
+  void* Y;
+  int nvec, ldx;
+  void* Xout;          // recurrence mode when non-null (may alias Xprev)
+  const void* Xprev;   // null on the first recurrence step
+  double a, cshift, b;
+};
+// variant v: vectors per CTA, threads per CTA, CTAs per SM the registers are sized for,
+// paired (1) or scalar (0) FP32 multiply-adds
+struct CellVariant { int vb, nt, minb, packed; };
+CellVariant cell_variant(int v);
+cudaError_t launch_cell_f32(const CellJob* jobs, int n, int variant, cudaStream_t s);
+// the same over systems of any orders in one persistent launch (systems of one order
+// must share the cell edges and the k-point, else cudaErrorInvalidValue)
+cudaError_t launch_cell_multi_f32(const CellJob* jobs, int n, cudaStream_t s);
 // single system, tile chosen by the context's tuned setting
 cudaError_t launch_hx_local_f64(const gbc_ctx* c, const double2* X, double2* Y, int nvec, int ldx,
                                 cudaStream_t s);
 cudaError_t launch_hx_local_f32(const gbc_ctx* c, const float2* X, float2* Y, int nvec, int ldx,
                                 cudaStream_t s);
-// nonlocal.cu : Y += sum_a P Delta P^H X
+// tc_cell.cu : Y += H^loc X for an FP32 block with the cell products as tcgen05
+// GEMMs (mode 0 TF32, 1 BF16x3); its bounded-wait flag (cleared on read)
+gbc_status tcl_apply(gbc_ctx* c, const float2* X, float2* Y, int nvec, int ldx, int mode,
+                     cudaStream_t s);
+cudaError_t tcl_error(int* err, cudaStream_t s);
+void tcl_free(TclState* t);
+// nonlocal.cu : Y += sum_a P Delta P^H X (overwrite: Y = sum_a P Delta P^H X on every
+// support row, other rows untouched)
 template <typename T>
 cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx,
-                            cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s);
+                            cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s, bool overwrite = false);
 // tcgen05 projector contractions (nonlocal_tc.cu), FP32 only
 bool tc_nonlocal_supported(const ProjDev& pj);
 cudaError_t launch_tc_project(const ProjDev& pj, long long M, const float2* X, int nvec, int ldx,
                               float2* Cbuf, cudaStream_t s);
 cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, const float2* Cp,
-                             cudaStream_t s);
+                             cudaStream_t s, bool overwrite = false);
 cudaError_t tc_nonlocal_reset(cudaStream_t s);
 cudaError_t tc_nonlocal_error(int* err, cudaStream_t s);
 
@@ -246,8 +280,33 @@ template <typename T>
 cudaError_t launch_cheb_step(const cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev,
                              cplx<T>* Xout, const T* invmd, long long M, int nvec, int ldx,
                              double a, double cshift, double b, cudaStream_t s);
-// batched recurrence update: one launch over several systems' blocks
+// the same update restricted to the listed rows (node indices), Y zeroed there
+template <typename T>
+cudaError_t launch_cheb_rows(cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev, cplx<T>* Xout,
+                             const T* invmd, const long long* rows, long long nrows, int nvec,
+                             int ldx, double a, double cshift, double b, cudaStream_t s);
+gbc_status setup_face_rows(gbc_ctx* c);
 #define GBC_MAX_CHEB_BATCH 32
+// the row update of several systems in one launch
+struct ChebRowsJob {
+  void* Y;
+  const void* Xcur;
+  const void* Xprev;   // may be null (first step)
+  void* Xout;
+  const void* invmd;
+  const long long* rows;
+  long long start;     // first flat element (listed row x spin x vector) of this job
+  int nvec, ldx;
+  double a, c, b;
+};
+struct ChebRowsBatch {
+  ChebRowsJob job[GBC_MAX_CHEB_BATCH];
+  int njobs;
+  long long total;
+};
+template <typename T>
+cudaError_t launch_cheb_rows_batch(const ChebRowsBatch& b, cudaStream_t s);
+// batched recurrence update: one launch over several systems' blocks
 struct ChebJob {
   void* Y;
   const void* Xcur;

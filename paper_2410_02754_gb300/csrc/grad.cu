@@ -24,7 +24,7 @@ namespace {
 
 inline unsigned gfor(long long n) {
   long long g = (n + 255) / 256;
-  return (unsigned)std::max(1LL, std::min(g, 152LL * 64));
+  return (unsigned)std::max(1LL, std::min(g, 64LL * gbc_sm_count()));
 }
 
 // Out[row][v] = w[row / 2] * In[row][v]

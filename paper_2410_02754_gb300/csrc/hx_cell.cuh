@@ -1,0 +1,723 @@
+// Cell-level apply of the local spinor Hamiltonian for FP32 blocks, with an
+// optional fused Chebyshev recurrence epilogue.
+//
+// Paper: Sec. IV.B.2 (extract X^(e) = R^(e) X, cell products, assemble
+// Y = sum_e R^(e)T Y^(e)) for the cell operator of Eq. FEHlocEl plus the k-terms
+// of Eq. FEHloc (per-cell Hermitian form), and Eq. chebfilt for the recurrence.
+// The arithmetic is the sum factorisation of the FP64 kernel (hx_local.cuh):
+// kinetic/k part K = G_x B_y B_z + B_x G_y B_z + B_x B_y G_z, potential part
+// N^T diag(w_q J [(V + |k|^2/2) I + B . sigma]) N, every 1-D operator in even-odd
+// form.  What differs is how it maps to the SM:
+//
+//  * complex values are float2 (re, im) and every real-matrix x complex-vector
+//    product is a paired FP32 multiply-add (one instruction for both parts);
+//  * per vector only three shared buffers: A (the gathered X^(e), n_p^3 nodes),
+//    T2 (n_p^3) and T1 (n_q^3 points), reused in place through the stages
+//      gather  X -> A
+//      Kz      A  -> T1 = B_z X, T2 = G_z X                     (z pencils)
+//      Ky      T1, T2 -> U1 = B_y T1, U2 = G_y T1 + B_y T2      (y pencils, in place)
+//      Kx+Ix   U1, U2, A -> T2 = G_x U1 + B_x U2 (kinetic result),
+//              T1 = N_x X                                       (x pencils, in place)
+//      Iy      T1 -> N_y T1                                     (y pencils, in place)
+//      Iz+W+Tz T1 -> N_z^T W N_z T1 with the 2x2 spin operator W at each point
+//              (z pencils; the two spins of a pencil on neighbouring lanes)
+//      Ty      T1 -> N_y^T T1                                   (y pencils, in place)
+//      Tx+out  T1 -> N_x^T T1 + T2, assembled                   (x pencils)
+//  * VB vectors per CTA, the vector index fastest across threads, so the gather
+//    and the scatter touch VB consecutive complex values of each node row; the
+//    gather of the next work item is issued (cp.async) as soon as A is free, so
+//    its latency hides behind the last four stages of the current item.
+//
+// Assembly modes (per system):
+//  * accumulate: Y += H^loc X with FP32 atomics on every node;
+//  * recurrence: for nodes interior to the cell (owned by it alone) the cell
+//    holds the complete local row, so the Chebyshev update is applied here:
+//      X_out = a (M_D^-1 (Y + y_loc) - c X) - b X_prev
+//    (Y holds the nonlocal term P C' of that row, written before this kernel,
+//    or zero); nodes on cell faces are accumulated into Y with atomics and
+//    finished by a separate row pass (launch_cheb_rows).
+#pragma once
+
+#include "hx_local.cuh"
+
+namespace gbc {
+
+// 1-D operator in even-odd form with every entry duplicated into a float2, the
+// multiplier of a paired multiply-add on (re, im)
+template <int NO, int NI> struct EO2 {
+  static constexpr int HO = (NO + 1) / 2;
+  static constexpr int HI = NI / 2 > 0 ? NI / 2 : 1;
+  float2 E[HO][HI];
+  float2 O[HO][HI];
+  float2 Mid[HO];
+};
+
+// PACKED: entries duplicated for paired multiply-adds; otherwise plain FP32
+// entries for two scalar multiply-adds (re, im) that take the entry straight
+// from the constant bank
+template <int NP, int NQ, bool PACKED> struct CellTables {
+  template <int NO, int NI>
+  using M = typename std::conditional<PACKED, EO2<NO, NI>, EO<float, NO, NI>>::type;
+  M<NP, NP> B[3];    // 1-D Gauss mass
+  M<NP, NP> Gr[3];   // 1/2 A_d
+  M<NP, NP> Gi[3];   // -1/2 k_d (C^ - C^T)
+  M<NQ, NP> Ni;      // interpolation to the Gauss points
+  M<NP, NQ> Nt;      // testing back to the nodes
+};
+
+// One system of a launch.
+struct CellSys {
+  const float2* X;      // block applied to
+  float2* Y;            // accumulator
+  const float* fields;  // [E][4][NQ^3] w_q J (V + |k|^2/2), w_q J B_x, B_y, B_z
+  float2* Xout;         // recurrence mode: X_{k+1} (may alias Xprev)
+  const float2* Xprev;  // recurrence mode: X_{k-1}, or null on the first step
+  const float* invmd;   // recurrence mode: 1 / M_D per node
+  float ca, cc, cb;     // recurrence mode: X_{k+1} = ca (M_D^-1 Y - cc X) - cb X_{k-1}
+  int ldx, nvec, vchunks, cheb;
+  long long item0;      // work items [item0, item0 + E * vchunks)
+  MeshDev mesh;
+};
+
+struct CellArgs {
+  CellSys sys[GBC_MAX_SYS];
+  int nsys;
+  long long nitems;
+};
+
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b, exactly (the fused product -1 * b is exact)
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {
+  return __ffma2_rn(make_float2(-1.f, -1.f), b, a);
+}
+__device__ __forceinline__ float2 p_mul(float2 m, float2 x) { return __fmul2_rn(m, x); }
+__device__ __forceinline__ float2 p_fma(float2 m, float2 x, float2 acc) {
+  return __ffma2_rn(m, x, acc);
+}
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+
+// 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// y = M x for a centro-symmetric (S = 1) or centro-antisymmetric (S = -1) M
+template <int S, int NO, int NI>
+__device__ __forceinline__ void eo2_apply(const EO2<NO, NI>& M, const float2 (&x)[NI],
+                                          float2 (&y)[NO]) {
+  constexpr int HI = NI / 2, HO = (NO + 1) / 2;
+  static_assert(HI >= 1, "NI >= 2");
+  float2 e[HI], o[HI];
+#pragma unroll
+  for (int j = 0; j < HI; ++j) {
+    e[j] = p_add(x[j], x[NI - 1 - j]);
+    o[j] = p_sub(x[j], x[NI - 1 - j]);
+  }
+#pragma unroll
+  for (int i = 0; i < HO; ++i) {
+    float2 ae = p_mul(M.E[i][0], e[0]);
+    float2 ao = p_mul(M.O[i][0], o[0]);
+#pragma unroll
+    for (int j = 1; j < HI; ++j) {
+      ae = p_fma(M.E[i][j], e[j], ae);
+      ao = p_fma(M.O[i][j], o[j], ao);
+    }
+    if (NI & 1) ae = p_fma(M.Mid[i], x[HI], ae);
+    y[i] = p_add(ae, ao);
+    if (NO - 1 - i != i) y[NO - 1 - i] = S > 0 ? p_sub(ae, ao) : p_sub(ao, ae);
+  }
+}
+
+// the same with plain FP32 entries: two scalar multiply-adds per complex product
+template <int S, int NO, int NI>
+__device__ __forceinline__ void eo2_apply(const EO<float, NO, NI>& M, const float2 (&x)[NI],
+                                          float2 (&y)[NO]) {
+  constexpr int HI = NI / 2, HO = (NO + 1) / 2;
+  static_assert(HI >= 1, "NI >= 2");
+  float2 e[HI], o[HI];
+#pragma unroll
+  for (int j = 0; j < HI; ++j) {
+    e[j] = make_float2(x[j].x + x[NI - 1 - j].x, x[j].y + x[NI - 1 - j].y);
+    o[j] = make_float2(x[j].x - x[NI - 1 - j].x, x[j].y - x[NI - 1 - j].y);
+  }
+#pragma unroll
+  for (int i = 0; i < HO; ++i) {
+    float er = M.E[i][0] * e[0].x, ei = M.E[i][0] * e[0].y;
+    float orr = M.O[i][0] * o[0].x, oi = M.O[i][0] * o[0].y;
+#pragma unroll
+    for (int j = 1; j < HI; ++j) {
+      er = fmaf(M.E[i][j], e[j].x, er);
+      ei = fmaf(M.E[i][j], e[j].y, ei);
+      orr = fmaf(M.O[i][j], o[j].x, orr);
+      oi = fmaf(M.O[i][j], o[j].y, oi);
+    }
+    if (NI & 1) {
+      er = fmaf(M.Mid[i], x[HI].x, er);
+      ei = fmaf(M.Mid[i], x[HI].y, ei);
+    }
+    y[i] = make_float2(er + orr, ei + oi);
+    if (NO - 1 - i != i)
+      y[NO - 1 - i] = S > 0 ? make_float2(er - orr, ei - oi) : make_float2(orr - er, oi - ei);
+  }
+}
+
+// y = (Gr + i Gi) x, Gr symmetric, Gi antisymmetric (Gi only at k != 0)
+template <bool KPT, int N, typename MT>
+__device__ __forceinline__ void g2_apply(const MT& Gr, const MT& Gi, const float2 (&x)[N],
+                                         float2 (&y)[N]) {
+  eo2_apply<1>(Gr, x, y);
+  if (KPT) {
+    float2 t[N];
+    eo2_apply<-1>(Gi, x, t);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = make_float2(y[i].x - t[i].y, y[i].y + t[i].x);
+  }
+}
+
+template <int NP, int NQ> __host__ __device__ constexpr int cell_vstride() {
+  // float2 elements per vector: [A | T2 | T1], two spins per point, padded to 8 mod 16
+  constexpr int n = 2 * (2 * pbuf_points<NP>() + pbuf_points<NQ>());
+  return n + ((24 - n % 16) % 16);
+}
+// vector buffers, then the node-offset tables of the current and the next work item
+template <int NP, int NQ, int VB> constexpr size_t hx_cell_smem() {
+  return sizeof(float2) * (size_t)VB * cell_vstride<NP, NQ>() + sizeof(int) * 2 * 3 * NP;
+}
+constexpr int kNoNode = -(1 << 29);   // offset of a direction with no free node (Dirichlet face)
+
+// The work items [0, nitems) of the systems sys[0 .. nsys) (item0 ascending), taken
+// first, first + stride, ... by this CTA.
+template <int NP, int NQ, bool KPT, int VB, int NT, bool PACKED>
+__device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int nsys,
+                                          long long nitems, const CellTables<NP, NQ, PACKED>& tb,
+                                          long long first, long long stride) {
+  constexpr int BA = pbuf_points<NP>();
+  constexpr int NQ3 = NQ * NQ * NQ;
+  constexpr int VS = cell_vstride<NP, NQ>();
+  extern __shared__ __align__(16) float2 sm[];
+  // spin s of point pidx of vector v: Buf(v)[2 * pidx + s]
+  auto Ab = [&](int v) { return sm + v * VS; };
+  auto T2b = [&](int v) { return sm + v * VS + 2 * BA; };
+  auto T1b = [&](int v) { return sm + v * VS + 4 * BA; };
+  auto pa = [](int x, int y, int z) { return pidx<NP>(x, y, z); };
+  auto pq = [](int x, int y, int z) { return pidx<NQ>(x, y, z); };
+  const int tid = threadIdx.x;
+  auto locate = [&](long long it) {
+    int q = 0;
+#pragma unroll
+    for (int r = 1; r < GBC_MAX_SYS; ++r)
+      if (r < nsys && it >= sys[r].item0) q = r;
+    return q;
+  };
+
+  // node index of local node (ix, iy, iz) of a work item's cell:
+  // noff[b][0][ix] + noff[b][1][iy] + noff[b][2][iz], negative where the node is
+  // on a Dirichlet face; b alternates between the current and the next item
+  int* noff = reinterpret_cast<int*>(sm + VB * VS);
+  auto offsets = [&](long long it, int b) {
+    if (tid < 3 * NP) {
+      const CellSys& g = sys[locate(it)];
+      const int e = (int)((it - g.item0) / g.vchunks);
+      const int dd = tid / NP, i = tid % NP;
+      const int c = dd == 0 ? e % g.mesh.ncell[0]
+                  : dd == 1 ? (e / g.mesh.ncell[0]) % g.mesh.ncell[1]
+                            : e / (g.mesh.ncell[0] * g.mesh.ncell[1]);
+      const int gc = c * g.mesh.p + i;
+      int f;
+      if (g.mesh.periodic[dd]) {
+        f = gc >= g.mesh.period[dd] ? gc - g.mesh.period[dd] : gc;
+      } else {
+        f = (gc == 0 || gc == g.mesh.period[dd]) ? -1 : gc - 1;
+      }
+      const int scale = dd == 0 ? 1 : dd == 1 ? g.mesh.nfree[0] : g.mesh.nfree[0] * g.mesh.nfree[1];
+      noff[b * 3 * NP + tid] = f < 0 ? kNoNode : f * scale;
+    }
+  };
+  // asynchronous gather of X^(e) of work item ``it`` into A: thread -> (vector,
+  // spin, node), vector fastest; absent nodes (Dirichlet faces) and vectors
+  // beyond nvec are zero-filled
+  auto gather = [&](long long it, int b) {
+    const CellSys& g = sys[locate(it)];
+    const int vb0 = (int)((it - g.item0) % g.vchunks) * VB;
+    const int* no = noff + b * 3 * NP;
+    for (int i = tid; i < VB * 2 * NP * NP * NP; i += NT) {
+      const int v = i % VB, r = i / VB, s = r & 1, n = r >> 1;
+      const int ix = n % NP, iy = (n / NP) % NP, iz = n / (NP * NP);
+      const int I = no[ix] + no[NP + iy] + no[2 * NP + iz];
+      const bool ok = I >= 0 && vb0 + v < g.nvec;
+      cp_async8(&Ab(v)[2 * pa(ix, iy, iz) + s],
+                ok ? &g.X[((long long)I * 2 + s) * g.ldx + vb0 + v] : g.X, ok ? 8 : 0);
+    }
+    cp_async_commit();
+  };
+
+  if (first < nitems) {
+    offsets(first, 0);
+    __syncthreads();
+    gather(first, 0);
+  }
+  int buf = 0;
+  for (long long item = first; item < nitems; item += stride, buf ^= 1) {
+    const CellSys& d = sys[locate(item)];
+    const long long li = item - d.item0;
+    const int e = (int)(li / d.vchunks);
+    const int vbase = (int)(li % d.vchunks) * VB;
+    const long long next = item + stride;
+    const int* no = noff + buf * 3 * NP;
+    cp_async_wait_all();
+    __syncthreads();
+    if (next < nitems) offsets(next, buf ^ 1);   // read after the next two barriers
+
+    // ---- Kz: T1 = B_z X, T2 = G_z X
+    for (int u = tid; u < VB * 2 * NP * NP; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int x = pen % NP, y = pen / NP;
+      float2 in[NP], t1[NP], t2[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) in[j] = Ab(v)[2 * pa(x, y, j) + s];
+      eo2_apply<1>(tb.B[2], in, t1);
+      g2_apply<KPT>(tb.Gr[2], tb.Gi[2], in, t2);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T1b(v)[2 * pq(x, y, i) + s] = t1[i];
+        T2b(v)[2 * pa(x, y, i) + s] = t2[i];
+      }
+    }
+    __syncthreads();
+
+    // ---- Ky (in place): U1 = B_y T1, U2 = G_y T1 + B_y T2
+    for (int u = tid; u < VB * 2 * NP * NP; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int x = pen % NP, z = pen / NP;
+      float2 t1[NP], t2[NP], u1[NP], u2[NP], w2[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        t1[j] = T1b(v)[2 * pq(x, j, z) + s];
+        t2[j] = T2b(v)[2 * pa(x, j, z) + s];
+      }
+      eo2_apply<1>(tb.B[1], t1, u1);
+      g2_apply<KPT>(tb.Gr[1], tb.Gi[1], t1, u2);
+      eo2_apply<1>(tb.B[1], t2, w2);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T1b(v)[2 * pq(x, i, z) + s] = u1[i];
+        T2b(v)[2 * pa(x, i, z) + s] = p_add(u2[i], w2[i]);
+      }
+    }
+    __syncthreads();
+
+    // ---- Kx + Ix (in place, x pencils): T2 = G_x U1 + B_x U2, T1 = N_x X
+    for (int u = tid; u < VB * 2 * NP * NP; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int y = pen % NP, z = pen / NP;
+      {
+        float2 u1[NP], u2[NP], yk[NP], w2[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          u1[j] = T1b(v)[2 * pq(j, y, z) + s];
+          u2[j] = T2b(v)[2 * pa(j, y, z) + s];
+        }
+        g2_apply<KPT>(tb.Gr[0], tb.Gi[0], u1, yk);
+        eo2_apply<1>(tb.B[0], u2, w2);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) T2b(v)[2 * pa(i, y, z) + s] = p_add(yk[i], w2[i]);
+      }
+      {
+        float2 in[NP], out[NQ];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) in[j] = Ab(v)[2 * pa(j, y, z) + s];
+        eo2_apply<1>(tb.Ni, in, out);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) T1b(v)[2 * pq(q, y, z) + s] = out[q];
+      }
+    }
+    __syncthreads();
+    // A is free from here on: start the next item's gather behind the remaining stages
+    if (next < nitems) gather(next, buf ^ 1);
+
+    // ---- Iy (in place): T1 (nq, np, np) -> (nq, nq, np)
+    for (int u = tid; u < VB * 2 * NQ * NP; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int x = pen % NQ, z = pen / NQ;
+      float2 in[NP], out[NQ];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) in[j] = T1b(v)[2 * pq(x, j, z) + s];
+      eo2_apply<1>(tb.Ni, in, out);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) T1b(v)[2 * pq(x, q, z) + s] = out[q];
+    }
+    __syncthreads();
+
+    // ---- Iz + spin operator + Tz (z pencils, in place); spin fastest, so the
+    // two spins of a pencil sit on neighbouring lanes and swap values by shuffle
+    {
+      const float* __restrict__ fld = d.fields + (size_t)e * 4 * NQ3;
+      constexpr int UNITS = VB * 2 * NQ * NQ;
+      constexpr int ROUNDS = (UNITS + NT - 1) / NT;
+#pragma unroll 1
+      for (int r = 0; r < ROUNDS; ++r) {
+        const int uu = tid + r * NT;
+        const bool act = uu < UNITS;
+        const int u = act ? uu : (uu & 1);
+        const int s = u & 1, v = (u >> 1) % VB, pen = (u >> 1) / VB;
+        const int x = pen % NQ, y = pen / NQ;
+        float2 in[NP], own[NQ];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) in[j] = T1b(v)[2 * pq(x, y, j) + s];
+        eo2_apply<1>(tb.Ni, in, own);
+        const float sg = s ? -1.f : 1.f;
+        float2 w[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          float2 oth;
+          oth.x = __shfl_xor_sync(0xffffffffu, own[q].x, 1);
+          oth.y = __shfl_xor_sync(0xffffffffu, own[q].y, 1);
+          const int qq = (q * NQ + y) * NQ + x;
+          const float V = __ldg(fld + qq), bx = __ldg(fld + NQ3 + qq),
+                      by = __ldg(fld + 2 * NQ3 + qq), bz = __ldg(fld + 3 * NQ3 + qq);
+          // up:   (V + bz) u + bx d + by (d.y, -d.x)
+          // down: (V - bz) d + bx u - by (u.y, -u.x)
+          float2 o = p_mul(dup(V + sg * bz), own[q]);
+          o = p_fma(dup(bx), oth, o);
+          w[q] = p_fma(make_float2(sg * by, -sg * by), make_float2(oth.y, oth.x), o);
+        }
+        float2 out[NP];
+        eo2_apply<1>(tb.Nt, w, out);
+        if (act) {
+#pragma unroll
+          for (int i = 0; i < NP; ++i) T1b(v)[2 * pq(x, y, i) + s] = out[i];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- Ty (in place): T1 (nq, nq, np) -> (nq, np, np)
+    for (int u = tid; u < VB * 2 * NQ * NP; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int x = pen % NQ, z = pen / NQ;
+      float2 in[NQ], out[NP];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) in[q] = T1b(v)[2 * pq(x, q, z) + s];
+      eo2_apply<1>(tb.Nt, in, out);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) T1b(v)[2 * pq(x, i, z) + s] = out[i];
+    }
+    __syncthreads();
+
+    // ---- Tx, add the kinetic part, assemble (vector fastest across threads)
+    for (int u = tid; u < VB * 2 * NP * NP; u += NT) {
+      const int v = u % VB, s = (u / VB) & 1, pen = u / (2 * VB);
+      const int y = pen % NP, z = pen / NP;
+      const int vec = vbase + v;
+      float2 in[NQ], out[NP];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) in[q] = T1b(v)[2 * pq(q, y, z) + s];
+      eo2_apply<1>(tb.Nt, in, out);
+      if (vec >= d.nvec) continue;
+      const bool yz_in = y > 0 && y < NP - 1 && z > 0 && z < NP - 1;
+      const int Iyz = no[NP + y] + no[2 * NP + z];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) out[i] = p_add(out[i], T2b(v)[2 * pa(i, y, z) + s]);
+      if (d.cheb && yz_in) {
+        // nodes x = 1 .. NP-2 of this pencil are interior to the cell: every load is
+        // issued before the first update (X_out may alias X_prev), so their latencies
+        // overlap
+        constexpr int NIN = NP - 2;
+        float2 yv[NIN], xv[NIN], pv[NIN];
+        float wv[NIN];
+#pragma unroll
+        for (int j = 0; j < NIN; ++j) {
+          const int I = Iyz + no[1 + j];
+          const long long o = ((long long)I * 2 + s) * d.ldx + vec;
+          yv[j] = d.Y[o];
+          xv[j] = __ldg(&d.X[o]);
+          wv[j] = __ldg(d.invmd + I);
+          pv[j] = d.Xprev ? d.Xprev[o] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < NIN; ++j) {
+          const int I = Iyz + no[1 + j];
+          const long long o = ((long long)I * 2 + s) * d.ldx + vec;
+          const float2 yt = p_add(yv[j], out[1 + j]);
+          const float2 xn = p_fma(dup(-d.cb), pv[j],
+                                  p_mul(dup(d.ca), p_fma(dup(-d.cc), xv[j], p_mul(dup(wv[j]), yt))));
+          d.Xout[o] = xn;
+        }
+#pragma unroll
+        for (int i = 0; i < NP; i += NP - 1) {   // the pencil's two face nodes
+          const int I = Iyz + no[i];
+          if (I >= 0) atomicAdd(&d.Y[((long long)I * 2 + s) * d.ldx + vec], out[i]);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const int I = Iyz + no[i];
+          if (I >= 0) atomicAdd(&d.Y[((long long)I * 2 + s) * d.ldx + vec], out[i]);
+        }
+      }
+    }
+  }
+}
+
+// one launch over systems that share p, the cell edges and the k-point
+template <int NP, int NQ, bool KPT, int VB, int NT, int MINB, bool PACKED>
+__global__ void __launch_bounds__(NT, MINB)
+hx_cell_kernel(const __grid_constant__ CellArgs a,
+               const __grid_constant__ CellTables<NP, NQ, PACKED> tb) {
+  cell_body<NP, NQ, KPT, VB, NT, PACKED>(a.sys, a.nsys, a.nitems, tb, blockIdx.x, gridDim.x);
+}
+
+// One persistent launch over systems of any order p: the systems are grouped by p
+// (each group shares the cell edges and the k-point), every group owns a range of
+// CTAs in proportion to its work, and each CTA runs the group's specialised body
+// over the group's items.
+struct CellGroup {
+  int p, kpt, s0, ns;      // order, k != 0, first system in CellMultiArgs::sys, count
+  int blk0, nblk;          // CTAs [blk0, blk0 + nblk)
+  long long nitems;
+};
+template <bool PACKED> struct CellMultiArgs {
+  CellSys sys[GBC_MAX_SYS];
+  CellGroup grp[GBC_MAX_P - 1];   // at most one group per order p = 2 .. GBC_MAX_P
+  int ngroups;
+  CellTables<3, 4, PACKED> t2;
+  CellTables<4, 5, PACKED> t3;
+  CellTables<5, 6, PACKED> t4;
+  CellTables<6, 7, PACKED> t5;
+  CellTables<7, 8, PACKED> t6;
+  CellTables<8, 9, PACKED> t7;
+};
+
+template <int VB, int NT, int MINB, bool PACKED>
+__global__ void __launch_bounds__(NT, MINB)
+hx_cell_multi_kernel(const __grid_constant__ CellMultiArgs<PACKED> m) {
+  int g = 0;
+  for (int i = 1; i < m.ngroups; ++i)
+    if ((int)blockIdx.x >= m.grp[i].blk0) g = i;
+  const CellGroup& G = m.grp[g];
+  const long long first = blockIdx.x - G.blk0, stride = G.nblk;
+  const CellSys* sys = m.sys + G.s0;
+#define GBC_CELL_BODY(P, T)                                                                    \
+  case P:                                                                                    \
+    if (G.kpt)                                                                               \
+      cell_body<P + 1, P + 2, true, VB, NT, PACKED>(sys, G.ns, G.nitems, m.T, first, stride);  \
+    else                                                                                     \
+      cell_body<P + 1, P + 2, false, VB, NT, PACKED>(sys, G.ns, G.nitems, m.T, first, stride); \
+    break;
+  switch (G.p) {
+    GBC_CELL_BODY(2, t2)
+    GBC_CELL_BODY(3, t3)
+    GBC_CELL_BODY(4, t4)
+    GBC_CELL_BODY(5, t5)
+    GBC_CELL_BODY(6, t6)
+    GBC_CELL_BODY(7, t7)
+    default: break;
+  }
+#undef GBC_CELL_BODY
+}
+
+template <int NO, int NI>
+inline void cvt_table(const EO<float, NO, NI>& src, EO<float, NO, NI>& dst) { dst = src; }
+template <int NO, int NI>
+inline void cvt_table(const EO<float, NO, NI>& src, EO2<NO, NI>& dst) {
+  for (int i = 0; i < EO2<NO, NI>::HO; ++i) {
+    for (int j = 0; j < EO2<NO, NI>::HI; ++j) {
+      dst.E[i][j] = make_float2(src.E[i][j], src.E[i][j]);
+      dst.O[i][j] = make_float2(src.O[i][j], src.O[i][j]);
+    }
+    dst.Mid[i] = make_float2(src.Mid[i], src.Mid[i]);
+  }
+}
+
+template <int NP, int NQ, bool PACKED>
+inline bool make_cell_tables(const gbc_ctx* c, CellTables<NP, NQ, PACKED>* t) {
+  TablesEO<float, NP, NQ> f;
+  if (!make_tables_eo<float, NP, NQ>(c, &f)) return false;
+  for (int d = 0; d < 3; ++d) {
+    cvt_table(f.B[d], t->B[d]);
+    cvt_table(f.Gr[d], t->Gr[d]);
+    cvt_table(f.Gi[d], t->Gi[d]);
+  }
+  cvt_table(f.Ni, t->Ni);
+  cvt_table(f.Nt, t->Nt);
+  return true;
+}
+
+// descriptor of one system (items numbered from item0)
+inline void fill_sys(CellSys& d, const CellJob& j, int vb, long long item0) {
+    const gbc_ctx* c = j.c;
+    d.X = (const float2*)j.X;
+    d.Y = (float2*)j.Y;
+    d.fields = c->d_fields32;
+    d.Xout = (float2*)j.Xout;
+    d.Xprev = (const float2*)j.Xprev;
+    d.invmd = c->d_invmd32;
+    d.ca = (float)j.a;
+    d.cc = (float)j.cshift;
+    d.cb = (float)j.b;
+    d.cheb = j.Xout != nullptr;
+    d.ldx = j.ldx;
+    d.nvec = j.nvec;
+    d.vchunks = (j.nvec + vb - 1) / vb;
+    d.item0 = item0;
+    d.mesh = c->mesh;
+}
+
+// One launch over up to GBC_MAX_SYS systems sharing p, the cell edges and the
+// k-point.
+template <int NP, int VB, int NT, int MINB, bool PACKED>
+cudaError_t launch_cell_group_p(const CellJob* jobs, int n, cudaStream_t s) {
+  constexpr int NQ = NP + 1;   // nq = p + 2
+  if (n < 1 || n > GBC_MAX_SYS) return cudaErrorInvalidValue;
+  CellArgs a;
+  long long item = 0;
+  for (int i = 0; i < GBC_MAX_SYS; ++i) {
+    CellSys& d = a.sys[i];
+    if (i >= n) {
+      d = a.sys[0];
+      d.item0 = 0x7fffffffffffffffLL;
+      continue;
+    }
+    fill_sys(d, jobs[i], VB, item);
+    item += (long long)jobs[i].c->mesh.E * d.vchunks;
+  }
+  a.nsys = n;
+  a.nitems = item;
+  if (item <= 0) return cudaSuccess;
+  const gbc_ctx* c0 = jobs[0].c;
+  CellTables<NP, NQ, PACKED> tb;
+  if (!make_cell_tables<NP, NQ, PACKED>(c0, &tb)) return cudaErrorInvalidValue;
+  const bool kpt = (c0->k[0] != 0.0 || c0->k[1] != 0.0 || c0->k[2] != 0.0);
+  constexpr size_t smem = hx_cell_smem<NP, NQ, VB>();
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (err != cudaSuccess) return err;
+  auto run = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long nblk = std::min<long long>(item, (long long)nsm * per_sm);
+    kern<<<(unsigned)nblk, NT, smem, s>>>(a, tb);
+    return cudaGetLastError();
+  };
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (kpt) return run(hx_cell_kernel<NP, NQ, true, VB, NT, MINB, PACKED>);
+  return run(hx_cell_kernel<NP, NQ, false, VB, NT, MINB, PACKED>);
+}
+
+template <bool PACKED>
+inline bool fill_multi_tables(CellMultiArgs<PACKED>& m, int p, const gbc_ctx* c) {
+  switch (p) {
+    case 2: return make_cell_tables<3, 4, PACKED>(c, &m.t2);
+    case 3: return make_cell_tables<4, 5, PACKED>(c, &m.t3);
+    case 4: return make_cell_tables<5, 6, PACKED>(c, &m.t4);
+    case 5: return make_cell_tables<6, 7, PACKED>(c, &m.t5);
+    case 6: return make_cell_tables<7, 8, PACKED>(c, &m.t6);
+    case 7: return make_cell_tables<8, 9, PACKED>(c, &m.t7);
+    default: return false;
+  }
+}
+template <int VB> constexpr size_t cell_smem_for_p(int p) {
+  return p == 2 ? hx_cell_smem<3, 4, VB>() : p == 3 ? hx_cell_smem<4, 5, VB>()
+       : p == 4 ? hx_cell_smem<5, 6, VB>() : p == 5 ? hx_cell_smem<6, 7, VB>()
+       : p == 6 ? hx_cell_smem<7, 8, VB>() : hx_cell_smem<8, 9, VB>();
+}
+
+// One persistent launch over up to GBC_MAX_SYS systems of any orders.  Systems of
+// one order must share the cell edges and the k-point (they share its tables);
+// otherwise cudaErrorInvalidValue and the caller launches per group.  CTAs are
+// split between the order groups in proportion to their estimated work
+// (cells x vector chunks x n_p^4 for the sum-factorised apply).
+template <int VB, int NT, int MINB, bool PACKED>
+cudaError_t launch_cell_multi(const CellJob* jobs, int n, cudaStream_t s) {
+  static_assert(sizeof(CellMultiArgs<PACKED>) <= 32764, "kernel parameter space");
+  if (n < 1 || n > GBC_MAX_SYS) return cudaErrorInvalidValue;
+  CellMultiArgs<PACKED> m;
+  m.ngroups = 0;
+  int k = 0;
+  double work[GBC_MAX_P - 1], wsum = 0;
+  size_t smem = 0;
+  for (int p = 2; p <= GBC_MAX_P; ++p) {
+    const gbc_ctx* c0 = nullptr;
+    long long item = 0;
+    const int s0 = k;
+    for (int i = 0; i < n; ++i) {
+      const gbc_ctx* c = jobs[i].c;
+      if (c->mesh.p != p) continue;
+      if (c->mesh.M >= (1LL << 29)) return cudaErrorInvalidValue;
+      if (!c0) {
+        c0 = c;
+      } else {
+        for (int d = 0; d < 3; ++d)
+          if (c->h[d] != c0->h[d] || c->k[d] != c0->k[d]) return cudaErrorInvalidValue;
+      }
+      fill_sys(m.sys[k], jobs[i], VB, item);
+      item += (long long)c->mesh.E * m.sys[k].vchunks;
+      ++k;
+    }
+    if (!c0 || item == 0) continue;
+    if (!fill_multi_tables<PACKED>(m, p, c0)) return cudaErrorInvalidValue;
+    CellGroup& G = m.grp[m.ngroups];
+    G.p = p;
+    G.kpt = (c0->k[0] != 0.0 || c0->k[1] != 0.0 || c0->k[2] != 0.0);
+    G.s0 = s0;
+    G.ns = k - s0;
+    G.nitems = item;
+    work[m.ngroups] = (double)item * std::pow((double)(p + 1), 4);
+    wsum += work[m.ngroups];
+    smem = std::max(smem, cell_smem_for_p<VB>(p));
+    ++m.ngroups;
+  }
+  for (int i = k; i < GBC_MAX_SYS; ++i) m.sys[i] = m.sys[0];
+  if (m.ngroups == 0) return cudaSuccess;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  auto kern = hx_cell_multi_kernel<VB, NT, MINB, PACKED>;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long total = (long long)nsm * per_sm;
+  long long blk = 0;
+  for (int g = 0; g < m.ngroups; ++g) {
+    CellGroup& G = m.grp[g];
+    long long nb = g + 1 == m.ngroups ? total - blk : (long long)std::llround(total * work[g] / wsum);
+    nb = std::max(1LL, std::min(nb, G.nitems));
+    G.blk0 = (int)blk;
+    G.nblk = (int)nb;
+    blk += nb;
+  }
+  kern<<<(unsigned)blk, NT, smem, s>>>(m);
+  return cudaGetLastError();
+}
+
+template <int VB, int NT, int MINB, bool PACKED>
+cudaError_t launch_cell_group(const CellJob* jobs, int n, cudaStream_t s) {
+  for (int i = 0; i < n; ++i)   // node offsets are 32-bit
+    if (jobs[i].c->mesh.M >= (1LL << 29)) return cudaErrorInvalidValue;
+  switch (jobs[0].c->mesh.p) {
+    case 2: return launch_cell_group_p<3, VB, NT, MINB, PACKED>(jobs, n, s);
+    case 3: return launch_cell_group_p<4, VB, NT, MINB, PACKED>(jobs, n, s);
+    case 4: return launch_cell_group_p<5, VB, NT, MINB, PACKED>(jobs, n, s);
+    case 5: return launch_cell_group_p<6, VB, NT, MINB, PACKED>(jobs, n, s);
+    case 6: return launch_cell_group_p<7, VB, NT, MINB, PACKED>(jobs, n, s);
+    case 7: return launch_cell_group_p<8, VB, NT, MINB, PACKED>(jobs, n, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gbc

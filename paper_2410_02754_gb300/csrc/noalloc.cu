@@ -86,6 +86,9 @@ extern "C" gbc_status gbc_apply_h_noalloc(gbc_ctx* c, const void* X, void* Y, in
     return gbc_fail(c, GBC_ESTATE,
                     "gbc_apply_h_noalloc: operator tables not built for the current fields/k-point/"
                     "projectors; call gbc_apply_h (or another hot-path call) once first");
+  if (c->prec == GBC_TF32 || c->prec == GBC_BF16X3)
+    return gbc_fail(c, GBC_EUNSUPPORTED,
+                    "gbc_apply_h_noalloc: the tensor-core cell apply needs library scratch");
   GBC_CU(c, cudaSetDevice(c->dev));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->prec == GBC_FP64) return apply_noalloc<double>(c, (const double2*)X, (double2*)Y, nvec, ldx, s);

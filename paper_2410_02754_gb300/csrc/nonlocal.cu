@@ -118,7 +118,7 @@ nl_expand(cplx<T>* __restrict__ Y, int ldx, int nvec, const int4* __restrict__ c
           const int* __restrict__ own_xptr, const int2* __restrict__ own_xinc,
           const cplx<T>* __restrict__ P, const int* __restrict__ atom_npj,
           const int* __restrict__ atom_pv_off, const int* __restrict__ atom_c_off,
-          const cplx<T>* __restrict__ Cp) {
+          const cplx<T>* __restrict__ Cp, int overwrite) {
   using C = cplx<T>;
   __shared__ C Ps[kExpStage][MAXPJ];
   const int4 ch = chunks[blockIdx.x];       // (atom, first owned index, count, -)
@@ -154,10 +154,14 @@ nl_expand(cplx<T>* __restrict__ Y, int ldx, int nvec, const int4* __restrict__ c
           for (int c = 0; c < nb2; ++c) cmac(acc, Pr[c], Cr[(size_t)(2 * c) * nvec]);
         }
         C* y = &Y[(own_node[u] * 2 + s) * ldx + v];
-        C o = *y;
-        o.x += acc.x;
-        o.y += acc.y;
-        *y = o;
+        if (overwrite) {
+          *y = acc;
+        } else {
+          C o = *y;
+          o.x += acc.x;
+          o.y += acc.y;
+          *y = o;
+        }
       }
     }
     __syncthreads();
@@ -183,7 +187,7 @@ bool use_tc(const gbc_ctx* c) { return c->nl_engine == GBC_NL_TENSOR && tc_nonlo
 
 template <typename T>
 cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx,
-                            cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s) {
+                            cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s, bool overwrite) {
   const ProjDev& pj = c->proj;
   if (pj.natoms == 0 || nvec == 0 || pj.nchunks == 0 || pj.nexp_chunks == 0) return cudaSuccess;
   cudaError_t e = launch_nl_project<T>(c, X, nvec, ldx, Cbuf, s);
@@ -196,7 +200,7 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if constexpr (std::is_same<T, float>::value) {
-    if (use_tc(c)) return launch_tc_expand(pj, Y, nvec, ldx, Cpbuf, s);
+    if (use_tc(c)) return launch_tc_expand(pj, Y, nvec, ldx, Cpbuf, s, overwrite);
   }
   const cplx<T>* P = std::is_same<T, double>::value ? (const cplx<T>*)pj.d_P64
                                                     : (const cplx<T>*)pj.d_P32;
@@ -204,7 +208,8 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
 #define GBC_EXPAND(MP)                                                                        \
   nl_expand<T, MP><<<g3, kCols, 0, s>>>(Y, ldx, nvec, pj.d_exp_chunks, pj.d_own_node,           \
                                         pj.d_own_pos, pj.d_own_xptr, pj.d_own_xinc, P,         \
-                                        pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off, Cpbuf)
+                                        pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off, Cpbuf, \
+                                        overwrite ? 1 : 0)
   if (pj.max_npj <= 4) GBC_EXPAND(4);
   else if (pj.max_npj <= 8) GBC_EXPAND(8);
   else if (pj.max_npj <= 18) GBC_EXPAND(18);
@@ -235,6 +240,6 @@ template cudaError_t launch_nl_project<double>(gbc_ctx*, const double2*, int, in
                                                cudaStream_t);
 
 template cudaError_t launch_nonlocal<float>(gbc_ctx*, const float2*, float2*, int, int, float2*,
-                                            float2*, cudaStream_t);
+                                            float2*, cudaStream_t, bool);
 template cudaError_t launch_nonlocal<double>(gbc_ctx*, const double2*, double2*, int, int,
-                                             double2*, double2*, cudaStream_t);
+                                             double2*, double2*, cudaStream_t, bool);

@@ -531,7 +531,8 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
             const int* __restrict__ own_pos, const int* __restrict__ own_xptr,
             const int2* __restrict__ own_xinc, const float2* __restrict__ P,
             const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off,
-            const int* __restrict__ atom_c_off, const float2* __restrict__ Cp, int chunk0) {
+            const int* __restrict__ atom_c_off, const float2* __restrict__ Cp, int chunk0,
+            int overwrite) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
   float4* Ahi = reinterpret_cast<float4*>(base);
@@ -642,7 +643,9 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int r = rbase + 8 * i;
-          if (r < cnt) yv[i] = *reinterpret_cast<const float4*>(Yr + s_node[r] * (long long)ncols + gc);
+          yv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (r < cnt && !overwrite)
+            yv[i] = *reinterpret_cast<const float4*>(Yr + s_node[r] * (long long)ncols + gc);
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -664,7 +667,7 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int c = gc + j;
-            if (c < ncols && ((c >> 1) % ldx) < nvec) y[j] += dv[j];
+            if (c < ncols && ((c >> 1) % ldx) < nvec) y[j] = overwrite ? dv[j] : y[j] + dv[j];
           }
         }
       }
@@ -777,7 +780,7 @@ cudaError_t launch_tc_project(const ProjDev& pj, long long M, const float2* X, i
 }
 
 cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, const float2* Cp,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool overwrite) {
   constexpr size_t smem = expand_smem();
   cudaError_t e =
       cudaFuncSetAttribute(k_tc_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -788,7 +791,8 @@ cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, co
     k_tc_expand<<<grid, 128, smem, s>>>(reinterpret_cast<float*>(Y), ldx, nvec, 2 * pj.max_npj,
                                         pj.d_tcexp_chunks, pj.d_tcexp_slots, pj.d_own_node,
                                         pj.d_own_pos, pj.d_own_xptr, pj.d_own_xinc, pj.d_P32,
-                                        pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off, Cp, c0);
+                                        pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off, Cp, c0,
+                                        overwrite ? 1 : 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -110,7 +110,7 @@ __global__ void k_mix(Hist h, int nh, Coef cf, double alpha, long long n,
 
 unsigned grid_for(long long n) {
   long long b = (n + 255) / 256;
-  return (unsigned)std::min<long long>(std::max<long long>(b, 1), 152LL * 8);
+  return (unsigned)std::min<long long>(std::max<long long>(b, 1), 8LL * gbc_sm_count());
 }
 
 }  // namespace

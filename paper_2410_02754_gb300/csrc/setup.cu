@@ -220,6 +220,33 @@ gbc_status setup_mass(gbc_ctx* c) {
   return GBC_OK;
 }
 
+// Free nodes on a cell face (a local index 0 or p in some direction): the rows
+// several cells add to.  In direction d the free index f is the global node
+// index g (periodic) or g - 1 (Dirichlet), and the node is on a face iff g % p == 0.
+gbc_status setup_face_rows(gbc_ctx* c) {
+  const MeshDev& m = c->mesh;
+  std::vector<char> face[3];
+  for (int d = 0; d < 3; ++d) {
+    face[d].assign(m.nfree[d], 0);
+    for (int f = 0; f < m.nfree[d]; ++f) {
+      const int g = m.periodic[d] ? f : f + 1;
+      face[d][f] = (g % m.p) == 0;
+    }
+  }
+  std::vector<long long> rows;
+  rows.reserve((size_t)(m.M / 2));
+  for (int z = 0; z < m.nfree[2]; ++z)
+    for (int y = 0; y < m.nfree[1]; ++y)
+      for (int x = 0; x < m.nfree[0]; ++x)
+        if (face[0][x] || face[1][y] || face[2][z])
+          rows.push_back(((long long)z * m.nfree[1] + y) * m.nfree[0] + x);
+  cudaFree(c->d_face_rows);
+  c->d_face_rows = nullptr;
+  c->nface = (long long)rows.size();
+  if (rows.empty()) return GBC_OK;
+  return upload(c, (void**)&c->d_face_rows, rows.data(), sizeof(long long) * rows.size());
+}
+
 gbc_status setup_fields(gbc_ctx* c) {
   const MeshDev& m = c->mesh;
   const int nq = c->nq;

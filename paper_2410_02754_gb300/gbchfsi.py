@@ -34,7 +34,8 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_tc_gemm_nt", "gbc_tc_wait_selftest", "gbc_set_nonlocal_engine", "gbc_get_nonlocal_engine",
            "gbc_sync_status", "gbc_density", "gbc_density_dev", "gbc_fermi_occupations",
            "gbc_prolongate", "gbc_scf_fields", "gbc_anderson_mix", "gbc_get_ndof",
-           "gbc_filter_backward"]
+           "gbc_filter_backward", "gbc_alu_peak", "gbc_set_cell_variant",
+           "gbc_get_cell_variant"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -101,6 +102,9 @@ def load_library(path: str = LIB_PATH):
         "gbc_get_nonlocal_engine": ([P, IP], I),
         "gbc_sync_status": ([P, V], I),
         "gbc_get_timing": ([P, I, DP, ct.POINTER(ct.c_longlong)], I),
+        "gbc_alu_peak": ([I, DP, DP, V], I),
+        "gbc_set_cell_variant": ([P, I], I),
+        "gbc_get_cell_variant": ([P, IP, IP, IP], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -443,7 +447,7 @@ class Context:
 
     # ---- tile autotuner -------------------------------------------------------------
     def tune(self, nvec, stream=None):
-        """Pick the FP32 cell-apply tile by timing; returns vectors per CTA."""
+        """Pick the FP32 cell-apply variant by timing; returns vectors per CTA."""
         self._chk(self.lib.gbc_tune(self.h, int(nvec), _stream_ptr(stream)))
         return self.tile()
 
@@ -451,6 +455,16 @@ class Context:
         v = ct.c_int()
         self._chk(self.lib.gbc_get_tile(self.h, ct.byref(v)))
         return v.value
+
+    def set_cell_variant(self, variant):
+        """Override the tuner's FP32 cell-apply variant (0 .. GBC_CELL_VARIANTS - 1)."""
+        self._chk(self.lib.gbc_set_cell_variant(self.h, int(variant)))
+
+    def cell_variant(self):
+        """(variant, vectors per CTA, threads per CTA) of the FP32 cell apply."""
+        v, vb, nt = ct.c_int(), ct.c_int(), ct.c_int()
+        self._chk(self.lib.gbc_get_cell_variant(self.h, ct.byref(v), ct.byref(vb), ct.byref(nt)))
+        return v.value, vb.value, nt.value
 
 
 class Batch:
@@ -518,6 +532,21 @@ def tc_gemm_nt(A, B, stream=None):
         raise GbcError(st, "gbc_tc_gemm_nt failed")
     return D
 
+
+
+PEAKS = {"ffma": 0, "ffma2": 1, "dfma": 2, "tf32": 3, "bf16": 4}
+
+
+def alu_peak(which, stream=None):
+    """Measured arithmetic rate of the current device: (FLOP/s, seconds of the timed
+    launch) for which in PEAKS (FP32 FMA, paired FP32 FMA, FP64 FMA, tcgen05 TF32 and
+    BF16 MMA)."""
+    rate, sec = ct.c_double(), ct.c_double()
+    st = load_library().gbc_alu_peak(int(PEAKS[which]), ct.byref(rate), ct.byref(sec),
+                                     _stream_ptr(stream))
+    if st != 0:
+        raise GbcError(st, f"gbc_alu_peak({which}) failed")
+    return rate.value, sec.value
 
 
 def tc_wait_selftest(max_iter=1000, stream=None):

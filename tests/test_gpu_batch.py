@@ -1,5 +1,6 @@
-"""Batched filtering of uneven systems (one persistent cell-apply launch per
-group, CUDA-graph replay) and the tile autotuner, against the FP64 oracle."""
+"""Batched filtering of uneven systems (FP32: one persistent cell-apply launch over
+systems of different orders; FP64: one per order group; CUDA-graph replay) and the
+cell-apply autotuner, against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -31,11 +32,18 @@ def g():
     return pkg
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
-def test_batch_filter_matches_oracle_and_replays(g, prec, tol):
+# a second p = 4 system at another k-point: the orders no longer map to one table set
+# each, so the FP32 path falls back to one launch per table group
+EXTRA = ((2, 2, 2), 4, (0.0, 0.2, 0.0), 1, 4, 4, 3, (1.5, 80.0, -2.0))
+
+
+@pytest.mark.parametrize("prec,tol,systems", [(0, 1e-11, SYSTEMS), (1, 2e-5, SYSTEMS),
+                                              (1, 2e-5, SYSTEMS + [EXTRA])],
+                         ids=["fp64", "fp32-one-launch", "fp32-grouped"])
+def test_batch_filter_matches_oracle_and_replays(g, prec, tol, systems):
     dt = torch.complex128 if prec == 0 else torch.complex64
     probs, ctxs, discs = [], [], []
-    for i, (nc, p, k, na, nv, ld, m, b) in enumerate(SYSTEMS):
+    for i, (nc, p, k, na, nv, ld, m, b) in enumerate(systems):
         prob = syn.make_problem(ncell=nc, h=(1.1, 1.1, 1.1), p=p, k=k, natoms=na, rc=1.2, seed=20 + i)
         c = g.Context(0)
         c.set_problem(prob)
@@ -47,7 +55,7 @@ def test_batch_filter_matches_oracle_and_replays(g, prec, tol):
     stream = torch.cuda.Stream()
     for call in range(2):                    # second call replays the captured graph
         Xs, refs = [], []
-        for i, (nc, p, k, na, nv, ld, m, b) in enumerate(SYSTEMS):
+        for i, (nc, p, k, na, nv, ld, m, b) in enumerate(systems):
             X = syn.random_block(discs[i].mesh.nnodes, nv, 100 * call + i)
             refs.append(oc.cheb_filter(discs[i].apply_htilde, X, m, *b))
             Xd = torch.zeros((X.shape[0], 2, ld), dtype=dt, device="cuda")
@@ -60,9 +68,9 @@ def test_batch_filter_matches_oracle_and_replays(g, prec, tol):
                 dst.copy_(src)
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
-            batch.filter(bufs, [s[6] for s in SYSTEMS], [s[7] for s in SYSTEMS], stream)
+            batch.filter(bufs, [s[6] for s in systems], [s[7] for s in systems], stream)
         stream.synchronize()
-        for i, s in enumerate(SYSTEMS):
+        for i, s in enumerate(systems):
             got = bufs[i].cpu().numpy()[:, :, :s[4]]
             assert rel(got, refs[i]) < tol, (call, i, rel(got, refs[i]))
     assert batch.launches() > 0
@@ -79,7 +87,9 @@ def test_tuner_picks_a_tile_and_keeps_parity(g):
     c.set_problem(prob)
     c.set_precision(1)
     vb = c.tune(8)
-    assert vb in (1, 2)
+    assert vb in (2, 4)
+    var, vb2, nt = c.cell_variant()
+    assert 0 <= var < 4 and vb2 == vb and nt in (256, 512)
     X = syn.random_block(d.mesh.nnodes, 8, 3)
     Xd = torch.from_numpy(X).to(torch.complex64).cuda()
     Yd = torch.empty_like(Xd)
@@ -87,4 +97,34 @@ def test_tuner_picks_a_tile_and_keeps_parity(g):
     torch.cuda.synchronize()
     assert rel(Yd.cpu().numpy(), d.apply_h(X)) < 1e-5
     assert c.tune(8) == vb                   # cached
+    c.close()
+
+
+def test_tuner_json_cache_and_nonlocal_engine(g, tmp_path, monkeypatch):
+    """The tuner's cache file is JSON: per key (device, FP32, p, k != 0, vector bucket) the
+    chosen cell-apply variant and nonlocal engine with the measured times of every
+    candidate; the context runs the chosen engine with parity kept."""
+    import json
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("GBC_TUNE_CACHE", str(path))
+    prob = syn.make_problem(ncell=(3, 3, 3), h=(1.0, 1.0, 1.0), p=4, k=(0.0, 0.1, 0.0), natoms=3,
+                            rc=1.5, seed=12, channels=syn.SPD_CHANNELS)
+    d = fe.Discretisation(prob)
+    c = g.Context(0)
+    c.set_problem(prob)
+    c.set_precision(1)
+    c.tune(40)                               # bucket nvec64: not tuned by the other tests
+    data = json.loads(path.read_text())
+    key = [k for k in data if k.endswith("/fp32/p4/k1/nvec64")]
+    assert len(key) == 1, list(data)
+    e = data[key[0]]
+    assert e["variant"] == c.cell_variant()[0]
+    assert e["nl_engine"] == c.nonlocal_engine() and e["nl_engine"] in (0, 1)
+    assert len(e["ms"]) == 4 and min(e["ms"]) > 0 and len(e["nl_ms"]) == 2
+    X = syn.random_block(d.mesh.nnodes, 40, 4)
+    Xd = torch.from_numpy(X).to(torch.complex64).cuda()
+    Yd = torch.empty_like(Xd)
+    c.apply_h(Xd, Yd)
+    c.sync_status()
+    assert rel(Yd.cpu().numpy(), d.apply_h(X)) < 1e-5
     c.close()
