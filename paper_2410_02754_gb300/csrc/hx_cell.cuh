@@ -179,9 +179,29 @@ __device__ __forceinline__ void g2_apply(const MT& Gr, const MT& Gi, const float
   }
 }
 
+// Point strides (y, z) of the n_p^3 buffers (A, T2) and of the n_q^3 buffer (T1).
+// With the unit order of the stages (vector fastest, then spin, then pencil) a
+// half-warp touches 4 pencils x 2 spins x 2 vectors; these strides put those 16
+// 8-byte accesses in 16 distinct bank pairs for every stage's pencil direction
+// (found by enumerating strides against a model of the 64-bit shared-memory
+// wavefronts); the n_p^3 buffers are dense for odd n_p.
+template <int NP> struct CellLayout;
+template <> struct CellLayout<3> { static constexpr int AY = 3, AZ = 9, QY = 5, QZ = 23; };
+template <> struct CellLayout<4> { static constexpr int AY = 5, AZ = 21, QY = 5, QZ = 25; };
+template <> struct CellLayout<5> { static constexpr int AY = 5, AZ = 25, QY = 9, QZ = 57; };
+template <> struct CellLayout<6> { static constexpr int AY = 7, AZ = 43, QY = 7, QZ = 51; };
+template <> struct CellLayout<7> { static constexpr int AY = 7, AZ = 49, QY = 9, QZ = 75; };
+template <> struct CellLayout<8> { static constexpr int AY = 9, AZ = 73, QY = 9, QZ = 81; };
+template <int NP> __host__ __device__ constexpr int cell_bufa() {   // points of A / T2
+  return (NP - 1) * (1 + CellLayout<NP>::AY + CellLayout<NP>::AZ) + 1;
+}
+template <int NP> __host__ __device__ constexpr int cell_bufq() {   // points of T1
+  return NP * (1 + CellLayout<NP>::QY + CellLayout<NP>::QZ) + 1;
+}
+
 template <int NP, int NQ> __host__ __device__ constexpr int cell_vstride() {
   // float2 elements per vector: [A | T2 | T1], two spins per point, padded to 8 mod 16
-  constexpr int n = 2 * (2 * pbuf_points<NP>() + pbuf_points<NQ>());
+  constexpr int n = 2 * (2 * cell_bufa<NP>() + cell_bufq<NP>());
   return n + ((24 - n % 16) % 16);
 }
 // vector buffers, then the node-offset tables of the current and the next work item
@@ -196,16 +216,17 @@ template <int NP, int NQ, bool KPT, int VB, int NT, bool PACKED>
 __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int nsys,
                                           long long nitems, const CellTables<NP, NQ, PACKED>& tb,
                                           long long first, long long stride) {
-  constexpr int BA = pbuf_points<NP>();
+  constexpr int BA = cell_bufa<NP>();
   constexpr int NQ3 = NQ * NQ * NQ;
   constexpr int VS = cell_vstride<NP, NQ>();
+  using L = CellLayout<NP>;
   extern __shared__ __align__(16) float2 sm[];
   // spin s of point pidx of vector v: Buf(v)[2 * pidx + s]
   auto Ab = [&](int v) { return sm + v * VS; };
   auto T2b = [&](int v) { return sm + v * VS + 2 * BA; };
   auto T1b = [&](int v) { return sm + v * VS + 4 * BA; };
-  auto pa = [](int x, int y, int z) { return pidx<NP>(x, y, z); };
-  auto pq = [](int x, int y, int z) { return pidx<NQ>(x, y, z); };
+  auto pa = [](int x, int y, int z) { return x + y * L::AY + z * L::AZ; };
+  auto pq = [](int x, int y, int z) { return x + y * L::QY + z * L::QZ; };
   const int tid = threadIdx.x;
   auto locate = [&](long long it) {
     int q = 0;

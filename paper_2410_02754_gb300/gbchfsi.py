@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgbchfsi.so")
 
 FP64, FP32 = 0, 1
-TF32, BF16X3 = 2, 3          # reserved: tensor-core cell apply, not built (GBC_EUNSUPPORTED)
+TF32, BF16X3 = 2, 3          # FP32 blocks, cell products as tcgen05 GEMMs (single TF32 / BF16 x3)
 STATUS = {0: "GBC_OK", 1: "GBC_EINVAL", 2: "GBC_ENOMEM", 3: "GBC_ECUDA", 4: "GBC_ESTATE",
           5: "GBC_ENOTPD", 6: "GBC_ETIMEOUT", 7: "GBC_EUNSUPPORTED"}
 
