@@ -184,10 +184,16 @@ def CELL_TRAFFIC(nvec):
     per32 = CELL_TRAFFIC_32
     if per32 is None:
         return None, "no ncu capture of this kernel version"
-    return per32 * nvec / 32, "ncu capture at 32 vectors (fused recurrence mode) scaled by vectors"
+    return (0.034e9 + (per32 - 0.034e9) * nvec / 32,
+            "ncu capture at 32 vectors (recurrence mode) scaled by vectors: 1.16x the "
+            "algorithmic bytes (X gather, interior Y / X_{k-1} reads and X_{k+1} writes, face-row "
+            "Y read-modify-write)")
 
 
-CELL_TRAFFIC_32 = None
+# DRAM bytes (read + write) of one recurrence-mode cell-apply launch on the cube16_p6 mesh at
+# 32 vectors, from the ncu capture in profiles/hx_cell_fused_cube16_p6_nvec32.md; 34 MB of it
+# are the fields (fixed), the rest grows with the vector count
+CELL_TRAFFIC_32 = 1.925e9
 
 
 def tc_cell_leg(g, prob, k, X, nvec, peaks, simt_ms):
@@ -465,6 +471,15 @@ def run_gpu(args):
         except Exception as exc:   # an auxiliary leg must not cost the headline line
             out["tc_cell"] = {"error": f"{type(exc).__name__}: {exc}"}
 
+    # ---- batch16 (config 2): sixteen uneven systems, one batched filter call per step
+    if not args.no_batch16 and rank == 0:
+        try:
+            r = batch16_measure(g, syn, args, steps=3, warmup=2)
+            r.pop("systems")
+            out["batch16"] = r
+        except Exception as exc:   # an auxiliary leg must not cost the headline line
+            out["batch16"] = {"error": f"{type(exc).__name__}: {exc}"}
+
     # ---- densities rho, m at the Gauss points from the filtered block (Eqs. rho, mag):
     # one gbc_density_dev launch on device-resident inputs, Fermi-Dirac occupations of the
     # block's Ritz values (N_e = nvec / 2 electrons, 500 K), timed with CUDA events
@@ -642,19 +657,13 @@ def run_gpu(args):
         print(json.dumps(out), flush=True)
 
 
-def run_batch(args):
-    """batch16: sixteen uneven systems filtered by one batched call per step
-    (persistent cell-apply launches per FE order, CUDA-graph replay)."""
+def batch16_measure(g, syn, args, clock_index=None, steps=None, warmup=None):
+    """batch16: sixteen uneven systems (8^3..14^3 cells, p in {4, 5, 6}, 64..320 vectors,
+    8..40 atoms, degree 12..24) filtered by one batched call per step: per degree one
+    persistent cell-apply launch over all systems (CTA groups per order), their nonlocal
+    steps and one face-row recurrence launch, the whole degree loop replayed as a CUDA
+    graph; beside it the same work as one gbc_filter call per system."""
     import torch
-
-    import __graft_entry__ as ge
-    import synthetic as syn
-    import paper_2410_02754_gb300 as g
-
-    rank, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "gloo")
-    _, _, local = dist_env()
-    torch.cuda.set_device(local)
-    ge.build()
     descs = syn.batch16_systems(0)
     ctxs, blocks, bounds, degrees, units = [], [], [], [], 0
     for d in descs:
@@ -675,22 +684,29 @@ def run_batch(args):
         bounds.append((float(r[-1]), hi, min(lo, float(r[0]))))
         degrees.append(d["degree"])
         units += M * d["nvec"] * d["degree"]
+    steps = steps or args.steps
+    warmup = warmup if warmup is not None else args.warmup
     batch = g.Batch(ctxs)
     stream = torch.cuda.Stream()
+    clocks = None
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             batch.filter(blocks, degrees, bounds, stream)
         stream.synchronize()
         dist_barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
-            e0.record(stream)
-            for _ in range(args.steps):
-                batch.filter(blocks, degrees, bounds, stream)
-            e1.record(stream)
-            stream.synchronize()
-        ms = dist_max(e0.elapsed_time(e1), "cuda" if world > 1 else "cpu") / args.steps
-        # the same work as one gbc_filter call per system (no batching, no graph)
+        sampler = ClockSampler(clock_index) if clock_index is not None else None
+        if sampler:
+            sampler.__enter__()
+        e0.record(stream)
+        for _ in range(steps):
+            batch.filter(blocks, degrees, bounds, stream)
+        e1.record(stream)
+        stream.synchronize()
+        if sampler:
+            sampler.__exit__()
+            clocks = sampler.summary()
+        ms = e0.elapsed_time(e1) / steps
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         for c, X, dg, b in zip(ctxs, blocks, degrees, bounds):
@@ -698,21 +714,44 @@ def run_batch(args):
         s1.record(stream)
         stream.synchronize()
         ms_seq = s0.elapsed_time(s1)
-    value = dist_sum(units, "cuda" if world > 1 else "cpu") / (ms / 1e3)
+    for c in ctxs:
+        c.sync_status()
+    res = {"units_per_step": units, "ms_per_step": ms, "value": units / (ms / 1e3), "unit": UNIT,
+           "systems": descs, "batched_graph_kernels_per_step": batch.launches(),
+           "tiles": [c.tile() for c in ctxs], "unbatched_ms_per_step": ms_seq,
+           "batching_speedup": ms_seq / ms, "clocks": clocks,
+           "how": f"{steps} batched filter calls after {warmup} warm-up, CUDA events on the "
+                  "batch stream; unbatched = one gbc_filter per system on the same stream"}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return res
+
+
+def run_batch(args):
+    """The batch16 workload as the bench line (--config batch16)."""
+    import __graft_entry__ as ge
+    import synthetic as syn
+    import paper_2410_02754_gb300 as g
+    import torch
+
+    rank, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "gloo")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    ge.build()
+    r = batch16_measure(g, syn, args, clock_index=local)
+    ms = dist_max(r["ms_per_step"], "cuda" if world > 1 else "cpu")
+    value = dist_sum(r["units_per_step"], "cuda" if world > 1 else "cpu") / (ms / 1e3)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "16 uneven periodic systems, 8^3..14^3 cells, p in {4,5,6}, "
                                   "64..320 vectors, 8..40 atoms x 18 projectors, degree 12..24",
-                      "config": "batch16", "systems": descs,
+                      "config": "batch16", "systems": r["systems"],
                       "l2": "inputs larger than L2"},
-           "batched_graph_kernels_per_step": batch.launches(),
-           "tiles": [c.tile() for c in ctxs],
-           "unbatched_ms_per_step": ms_seq, "batching_speedup": ms_seq / ms,
-           "clocks": clk.summary()}
-    batch.close()
-    for c in ctxs:
-        c.close()
+           "batched_graph_kernels_per_step": r["batched_graph_kernels_per_step"],
+           "tiles": r["tiles"], "unbatched_ms_per_step": r["unbatched_ms_per_step"],
+           "batching_speedup": r["batching_speedup"], "clocks": r["clocks"]}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -972,6 +1011,7 @@ def main():
     ap.add_argument("--no-density", action="store_true")
     ap.add_argument("--no-twogrid", action="store_true")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core cell-apply leg")
+    ap.add_argument("--no-batch16", action="store_true", help="skip the batch16 leg")
     ap.add_argument("--scf-steps", type=int, default=2, help="SCF steps of the scf leg (0: off)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

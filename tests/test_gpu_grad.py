@@ -146,3 +146,67 @@ def test_full_size_c1_mesh_gradients_vs_fd(g):
     assert rel(GX32.cpu().numpy(), GX.cpu().numpy()) < 1e-4
     assert rel(f32[0], fV) < 1e-4
     c.close()
+
+
+def test_full_size_fifty_direction_fd(g, capsys):
+    """Config 3's check at the full cube16_p6 mesh (884,736 nodes, 64 atoms x 18 SOC
+    projectors, k != 0; 4 vectors, degree 20, checkpoints every 5, FP64): along 50
+    seeded unit-norm joint directions in (V_eff, B_x, B_y, B_z at every Gauss point, every
+    Hermitian Delta_a, the input block) the central difference of the loss at step 1e-6
+    agrees with the gradient's directional derivative to 1e-6 relative.  The loss's own
+    run-to-run reproducibility is printed beside it."""
+    prob = syn.config("cube16_p6", kindex=0)
+    c = g.Context(0)
+    c.set_problem(prob)
+    M = prob.nnodes
+    rng = np.random.default_rng(50)
+    X0 = syn.random_block(M, 4, 9)
+    w = rng.uniform(0, 1, 4)
+    lo, lmax = c.lanczos_bounds(torch.from_numpy(syn.random_start(M, 1)).cuda(), 10)
+    lmin, lT = min(lo, -1.0), lo + 5.0
+    fields0 = [np.array(a) for a in (prob.veff, prob.bx, prob.by, prob.bz)]
+    delta0 = np.concatenate([a.delta.reshape(-1) for a in prob.atoms])
+
+    def loss(t=0.0, dirn=None):
+        if dirn is None:
+            f, dl, X = fields0, delta0, X0
+        else:
+            f = [a + t * b for a, b in zip(fields0, dirn[0])]
+            dl, X = delta0 + t * dirn[1], X0 + t * dirn[2]
+        c.set_fields(*f)
+        c.set_delta(dl)
+        Xd = torch.from_numpy(X).cuda()
+        c.filter(Xd, 20, lT, lmax, lmin)
+        return c.energy_grad(Xd, w, torch.empty_like(Xd))[0], Xd
+
+    L, Yd = loss()
+    GYd = torch.empty_like(Yd)
+    _, gV, gBx, gBy, gBz, gD = c.energy_grad(Yd, w, GYd)
+    X0d = torch.from_numpy(X0).cuda()
+    GX = torch.empty_like(X0d)
+    fV, fBx, fBy, fBz, fD = c.filter_vjp(X0d, GYd, GX, 20, lT, lmax, lmin, ckpt_every=5)
+    gf = [gV + fV, gBx + fBx, gBy + fBy, gBz + fBz]
+    gDt, gXt = gD + fD, GX.cpu().numpy()
+    noise = abs(loss()[0] - L) / abs(L)
+    h, worst = 1e-6, 0.0
+    nd = [a.delta.shape[0] for a in prob.atoms]
+    for trial in range(50):
+        df = [rng.normal(size=a.shape) for a in fields0]
+        E = rng.normal(size=delta0.shape) + 1j * rng.normal(size=delta0.shape)
+        E = np.concatenate([0.5 * (B + B.conj().T).reshape(-1) for B, n in
+                            zip(np.split(E, np.cumsum([n * n for n in nd])[:-1]), nd)
+                            for B in [B.reshape(n, n)]])
+        D = rng.normal(size=X0.shape) + 1j * rng.normal(size=X0.shape)
+        # unit-norm joint direction, so h is the size of the step in parameter space
+        nrm = np.sqrt(sum(np.sum(a * a) for a in df) + np.sum(np.abs(E) ** 2) + np.sum(np.abs(D) ** 2))
+        df, E, D = [a / nrm for a in df], E / nrm, D / nrm
+        dirn = (df, E, D)
+        num = (loss(h, dirn)[0] - loss(-h, dirn)[0]) / (2 * h)
+        ana = (sum(float(np.sum(a * b)) for a, b in zip(gf, df))
+               + float(np.real(np.sum(gDt.conj() * E))) + float(np.real(np.sum(gXt.conj() * D))))
+        worst = max(worst, abs(num - ana) / abs(num))
+    c.close()
+    with capsys.disabled():
+        print(f"  full-size FD, 50 joint directions, h = {h:g}: worst relative error {worst:.2e}; "
+              f"loss reproducibility {noise:.1e}")
+    assert worst <= 1e-6, worst
