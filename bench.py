@@ -660,9 +660,10 @@ def run_gpu(args):
 def batch16_measure(g, syn, args, clock_index=None, steps=None, warmup=None):
     """batch16: sixteen uneven systems (8^3..14^3 cells, p in {4, 5, 6}, 64..320 vectors,
     8..40 atoms, degree 12..24) filtered by one batched call per step: per degree one
-    persistent cell-apply launch over all systems (CTA groups per order), their nonlocal
-    steps and one face-row recurrence launch, the whole degree loop replayed as a CUDA
-    graph; beside it the same work as one gbc_filter call per system."""
+    persistent cell-apply launch per group of systems sharing order, cell edges and
+    k-point, their nonlocal steps and one face-row recurrence launch, the whole degree
+    loop replayed as a CUDA graph; beside it the same work as one gbc_filter call per
+    system."""
     import torch
     descs = syn.batch16_systems(0)
     ctxs, blocks, bounds, degrees, units = [], [], [], [], 0

@@ -326,8 +326,8 @@ const char* gbc_batch_last_error(const gbc_batch* batch);
  * X[i] is system i's block ([M_i][2][ldx[i]], the context precision), filtered
  * in place to degree[i] with bounds[3i..3i+2] = (lT, lmax, lmin).  Systems that
  * share the FE order, cell edges and k-point run their cell-level applies in
- * one persistent launch (up to 8 per launch); the recurrence updates of all
- * systems run in one launch per degree.  The whole degree loop is captured in a
+ * one persistent launch (up to 16 per launch); in FP32 the cell-face rows of all
+ * systems are finished in one launch per degree, in FP64 the recurrence updates.  The whole degree loop is captured in a
  * CUDA graph on the first call and replayed by later calls with the same
  * arguments (pointers, sizes, degrees, bounds); other arguments re-capture.
  * ``stream`` must be a created stream, not the legacy default stream (stream
@@ -356,7 +356,8 @@ gbc_status gbc_get_tile(const gbc_ctx* ctx, int* vectors_per_cta);
  * GBC_CELL_VARIANTS - 1: 0 = 2 vectors x 256 threads with registers for 4 CTAs
  * per SM, paired FP32 multiply-adds on (re, im); 1 = the same tile with
  * registers for 3 CTAs per SM; 2 and 3 = variants 0 and 1 with scalar FP32
- * multiply-adds.  gbc_get_cell_variant
+ * multiply-adds.  (One vector x 128 threads per CTA measured 1.5-2.5x slower at
+ * p = 6 and is not compiled.)  gbc_get_cell_variant
  * also returns the variant's vectors and threads per CTA (either pointer may be
  * NULL).  GBC_EINVAL for a variant out of range. */
 #define GBC_CELL_VARIANTS 4

@@ -436,7 +436,9 @@ gbc_status gbc_create(gbc_ctx** out, int device_ordinal) {
   gbc_ctx* c = new (std::nothrow) gbc_ctx();
   if (!c) return GBC_ENOMEM;
   c->dev = device_ordinal;
-  if (cudaSetDevice(device_ordinal) != cudaSuccess || cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess) {
+  if (cudaSetDevice(device_ordinal) != cudaSuccess || cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_cell_ctr, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaFree(c->d_flag);
     delete c;
     return GBC_ECUDA;
   }
@@ -458,7 +460,7 @@ void gbc_destroy(gbc_ctx* c) {
   void* ptrs[] = {c->d_md, c->d_invmd, c->d_invmd32, c->d_rawfields, c->d_fields64, c->d_fields32,
                   c->work[0], c->work[1], c->work[2], c->work[3], c->work[4], c->work[5],
                   c->work[6], c->work[7], c->work[8], c->work[9], c->d_small, c->d_flag,
-                  c->d_face_rows};
+                  c->d_face_rows, c->d_cell_ctr};
   for (void* p : ptrs) cudaFree(p);
   delete c;
 }

@@ -45,7 +45,7 @@ namespace {
 // the times that chose them
 struct TuneEntry {
   int variant = 0, nl_engine = -1;   // nl_engine -1: not tuned (no atoms)
-  float ms[GBC_CELL_VARIANTS] = {0, 0, 0, 0};
+  float ms[GBC_CELL_VARIANTS] = {};
   float nl_ms[2] = {0, 0};
 };
 
@@ -68,6 +68,7 @@ void tune_load() {
   FILE* fp = std::fopen(f.c_str(), "r");
   if (!fp) return;
   char line[1024];
+  static_assert(GBC_CELL_VARIANTS == 4, "the cache line format lists four variant times");
   while (std::fgets(line, sizeof line, fp)) {
     char key[512];
     TuneEntry e;
@@ -318,9 +319,9 @@ gbc_status record_filters(gbc_batch* b, std::vector<SysRun>& runs, cudaStream_t 
         *a = k == 0 ? r.sig[0] / r.e : 2.0 * r.sig[k] / r.e;
         *bb = k == 0 ? 0.0 : r.sig[k - 1] * r.sig[k];
       };
-      // the cell applies of every active system, whatever its order, in one
-      // persistent launch (per-order groups of CTAs); per-table-group launches only
-      // when systems of one order differ in cell edges or k-point
+      // the cell applies: one launch per group of systems sharing the tables (order,
+      // cell edges, k-point) and the tuned variant, each a persistent launch whose
+      // CTAs share the group's work counter
       std::vector<CellJob> all;
       for (int i : active) {
         void *cur, *prev, *out;
@@ -329,27 +330,19 @@ gbc_status record_filters(gbc_batch* b, std::vector<SysRun>& runs, cudaStream_t 
         all.push_back(CellJob{runs[i].c, cur, runs[i].Y, runs[i].nvec, runs[i].ldx, out, prev, a,
                               runs[i].cc, bb});
       }
-      cudaError_t em = cudaErrorInvalidValue;
-      if ((int)all.size() <= GBC_MAX_SYS) em = launch_cell_multi_f32(all.data(), (int)all.size(), s);
-      if (em == cudaSuccess) {
-        ++count;
-      } else if (em != cudaErrorInvalidValue) {
-        return bfail(b, GBC_ECUDA, std::string("cell apply: ") + cudaGetErrorString(em));
-      } else {
-        std::vector<bool> done(all.size(), false);
-        for (size_t i = 0; i < all.size(); ++i) {
-          if (done[i]) continue;
-          std::vector<CellJob> jobs;
-          for (size_t j = i; j < all.size() && (int)jobs.size() < GBC_MAX_SYS; ++j) {
-            if (done[j] || !same_tables(all[i].c, all[j].c) || all[i].c->cell_var != all[j].c->cell_var)
-              continue;
-            jobs.push_back(all[j]);
-            done[j] = true;
-          }
-          const cudaError_t e = launch_cell_f32(jobs.data(), (int)jobs.size(), all[i].c->cell_var, s);
-          if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("cell apply: ") + cudaGetErrorString(e));
-          ++count;
+      std::vector<bool> done(all.size(), false);
+      for (size_t i = 0; i < all.size(); ++i) {
+        if (done[i]) continue;
+        std::vector<CellJob> jobs;
+        for (size_t j = i; j < all.size() && (int)jobs.size() < GBC_MAX_SYS; ++j) {
+          if (done[j] || !same_tables(all[i].c, all[j].c) || all[i].c->cell_var != all[j].c->cell_var)
+            continue;
+          jobs.push_back(all[j]);
+          done[j] = true;
         }
+        const cudaError_t e = launch_cell_f32(jobs.data(), (int)jobs.size(), all[i].c->cell_var, s);
+        if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("cell apply: ") + cudaGetErrorString(e));
+        ++count;
       }
       // cell-face rows of every active system, one launch
       for (size_t a0 = 0; a0 < active.size(); a0 += GBC_MAX_CHEB_BATCH) {

@@ -155,6 +155,7 @@ struct gbc_ctx {
   void* d_small = nullptr;           // small dense scratch (Gram, eigensolver)
   size_t small_bytes = 0;
   int* d_flag = nullptr;
+  unsigned long long* d_cell_ctr = nullptr;   // work counter of the FP32 cell-apply launches
   int vb32 = 2;                      // FP64 kernel tile (vectors per CTA; fixed)
   int cell_var = 0;                  // FP32 cell-apply variant (GBC_CELL_VARIANTS), set by the tuner
   long long nface = 0;               // free nodes on cell faces (shared by several cells)
@@ -235,9 +236,6 @@ struct CellJob {
 struct CellVariant { int vb, nt, minb, packed; };
 CellVariant cell_variant(int v);
 cudaError_t launch_cell_f32(const CellJob* jobs, int n, int variant, cudaStream_t s);
-// the same over systems of any orders in one persistent launch (systems of one order
-// must share the cell edges and the k-point, else cudaErrorInvalidValue)
-cudaError_t launch_cell_multi_f32(const CellJob* jobs, int n, cudaStream_t s);
 // single system, tile chosen by the context's tuned setting
 cudaError_t launch_hx_local_f64(const gbc_ctx* c, const double2* X, double2* Y, int nvec, int ldx,
                                 cudaStream_t s);

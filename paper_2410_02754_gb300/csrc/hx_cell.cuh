@@ -206,16 +206,18 @@ template <int NP, int NQ> __host__ __device__ constexpr int cell_vstride() {
 }
 // vector buffers, then the node-offset tables of the current and the next work item
 template <int NP, int NQ, int VB> constexpr size_t hx_cell_smem() {
-  return sizeof(float2) * (size_t)VB * cell_vstride<NP, NQ>() + sizeof(int) * 2 * 3 * NP;
+  return sizeof(float2) * (size_t)VB * cell_vstride<NP, NQ>() + sizeof(int) * 2 * 3 * NP + 16;
 }
 constexpr int kNoNode = -(1 << 29);   // offset of a direction with no free node (Dirichlet face)
 
 // The work items [0, nitems) of the systems sys[0 .. nsys) (item0 ascending), taken
-// first, first + stride, ... by this CTA.
+// from the counter *ctr (zero at launch) one atomic increment at a time, so CTAs
+// that finish early take more and the items in flight stay close to each other in
+// the order (cell-major, vector chunks of a cell adjacent).
 template <int NP, int NQ, bool KPT, int VB, int NT, bool PACKED>
 __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int nsys,
                                           long long nitems, const CellTables<NP, NQ, PACKED>& tb,
-                                          long long first, long long stride) {
+                                          unsigned long long* __restrict__ ctr) {
   constexpr int BA = cell_bufa<NP>();
   constexpr int NQ3 = NQ * NQ * NQ;
   constexpr int VS = cell_vstride<NP, NQ>();
@@ -277,21 +279,30 @@ __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int n
     cp_async_commit();
   };
 
+  // the next item's index; tid 0 writes it before a barrier that every thread
+  // passes after its last read of the previous value (the stage barriers below)
+  long long* s_next = reinterpret_cast<long long*>(noff + 2 * 3 * NP);
+  if (tid == 0) *s_next = (long long)atomicAdd(ctr, 1ULL);
+  __syncthreads();
+  const long long first = *s_next;
+  __syncthreads();
   if (first < nitems) {
     offsets(first, 0);
     __syncthreads();
     gather(first, 0);
   }
   int buf = 0;
-  for (long long item = first; item < nitems; item += stride, buf ^= 1) {
+  long long next = first;
+  for (long long item = first; item < nitems; item = next, buf ^= 1) {
     const CellSys& d = sys[locate(item)];
     const long long li = item - d.item0;
     const int e = (int)(li / d.vchunks);
     const int vbase = (int)(li % d.vchunks) * VB;
-    const long long next = item + stride;
     const int* no = noff + buf * 3 * NP;
+    if (tid == 0) *s_next = (long long)atomicAdd(ctr, 1ULL);
     cp_async_wait_all();
     __syncthreads();
+    next = *s_next;
     if (next < nitems) offsets(next, buf ^ 1);   // read after the next two barriers
 
     // ---- Kz: T1 = B_z X, T2 = G_z X
@@ -485,61 +496,14 @@ __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int n
   }
 }
 
-// one launch over systems that share p, the cell edges and the k-point
+// One persistent launch over systems that share p, the cell edges and the k-point;
+// the CTAs take their work items from the zeroed counter *ctr in ascending order.
 template <int NP, int NQ, bool KPT, int VB, int NT, int MINB, bool PACKED>
 __global__ void __launch_bounds__(NT, MINB)
 hx_cell_kernel(const __grid_constant__ CellArgs a,
-               const __grid_constant__ CellTables<NP, NQ, PACKED> tb) {
-  cell_body<NP, NQ, KPT, VB, NT, PACKED>(a.sys, a.nsys, a.nitems, tb, blockIdx.x, gridDim.x);
-}
-
-// One persistent launch over systems of any order p: the systems are grouped by p
-// (each group shares the cell edges and the k-point), every group owns a range of
-// CTAs in proportion to its work, and each CTA runs the group's specialised body
-// over the group's items.
-struct CellGroup {
-  int p, kpt, s0, ns;      // order, k != 0, first system in CellMultiArgs::sys, count
-  int blk0, nblk;          // CTAs [blk0, blk0 + nblk)
-  long long nitems;
-};
-template <bool PACKED> struct CellMultiArgs {
-  CellSys sys[GBC_MAX_SYS];
-  CellGroup grp[GBC_MAX_P - 1];   // at most one group per order p = 2 .. GBC_MAX_P
-  int ngroups;
-  CellTables<3, 4, PACKED> t2;
-  CellTables<4, 5, PACKED> t3;
-  CellTables<5, 6, PACKED> t4;
-  CellTables<6, 7, PACKED> t5;
-  CellTables<7, 8, PACKED> t6;
-  CellTables<8, 9, PACKED> t7;
-};
-
-template <int VB, int NT, int MINB, bool PACKED>
-__global__ void __launch_bounds__(NT, MINB)
-hx_cell_multi_kernel(const __grid_constant__ CellMultiArgs<PACKED> m) {
-  int g = 0;
-  for (int i = 1; i < m.ngroups; ++i)
-    if ((int)blockIdx.x >= m.grp[i].blk0) g = i;
-  const CellGroup& G = m.grp[g];
-  const long long first = blockIdx.x - G.blk0, stride = G.nblk;
-  const CellSys* sys = m.sys + G.s0;
-#define GBC_CELL_BODY(P, T)                                                                    \
-  case P:                                                                                    \
-    if (G.kpt)                                                                               \
-      cell_body<P + 1, P + 2, true, VB, NT, PACKED>(sys, G.ns, G.nitems, m.T, first, stride);  \
-    else                                                                                     \
-      cell_body<P + 1, P + 2, false, VB, NT, PACKED>(sys, G.ns, G.nitems, m.T, first, stride); \
-    break;
-  switch (G.p) {
-    GBC_CELL_BODY(2, t2)
-    GBC_CELL_BODY(3, t3)
-    GBC_CELL_BODY(4, t4)
-    GBC_CELL_BODY(5, t5)
-    GBC_CELL_BODY(6, t6)
-    GBC_CELL_BODY(7, t7)
-    default: break;
-  }
-#undef GBC_CELL_BODY
+               const __grid_constant__ CellTables<NP, NQ, PACKED> tb,
+               unsigned long long* __restrict__ ctr) {
+  cell_body<NP, NQ, KPT, VB, NT, PACKED>(a.sys, a.nsys, a.nitems, tb, ctr);
 }
 
 template <int NO, int NI>
@@ -620,6 +584,8 @@ cudaError_t launch_cell_group_p(const CellJob* jobs, int n, cudaStream_t s) {
   if (err != cudaSuccess) return err;
   err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (err != cudaSuccess) return err;
+  unsigned long long* ctr = c0->d_cell_ctr;   // the first system's work counter
+  if (!ctr) return cudaErrorInvalidValue;
   auto run = [&](auto kern) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -627,103 +593,14 @@ cudaError_t launch_cell_group_p(const CellJob* jobs, int n, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long nblk = std::min<long long>(item, (long long)nsm * per_sm);
-    kern<<<(unsigned)nblk, NT, smem, s>>>(a, tb);
+    e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nblk, NT, smem, s>>>(a, tb, ctr);
     return cudaGetLastError();
   };
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (kpt) return run(hx_cell_kernel<NP, NQ, true, VB, NT, MINB, PACKED>);
   return run(hx_cell_kernel<NP, NQ, false, VB, NT, MINB, PACKED>);
-}
-
-template <bool PACKED>
-inline bool fill_multi_tables(CellMultiArgs<PACKED>& m, int p, const gbc_ctx* c) {
-  switch (p) {
-    case 2: return make_cell_tables<3, 4, PACKED>(c, &m.t2);
-    case 3: return make_cell_tables<4, 5, PACKED>(c, &m.t3);
-    case 4: return make_cell_tables<5, 6, PACKED>(c, &m.t4);
-    case 5: return make_cell_tables<6, 7, PACKED>(c, &m.t5);
-    case 6: return make_cell_tables<7, 8, PACKED>(c, &m.t6);
-    case 7: return make_cell_tables<8, 9, PACKED>(c, &m.t7);
-    default: return false;
-  }
-}
-template <int VB> constexpr size_t cell_smem_for_p(int p) {
-  return p == 2 ? hx_cell_smem<3, 4, VB>() : p == 3 ? hx_cell_smem<4, 5, VB>()
-       : p == 4 ? hx_cell_smem<5, 6, VB>() : p == 5 ? hx_cell_smem<6, 7, VB>()
-       : p == 6 ? hx_cell_smem<7, 8, VB>() : hx_cell_smem<8, 9, VB>();
-}
-
-// One persistent launch over up to GBC_MAX_SYS systems of any orders.  Systems of
-// one order must share the cell edges and the k-point (they share its tables);
-// otherwise cudaErrorInvalidValue and the caller launches per group.  CTAs are
-// split between the order groups in proportion to their estimated work
-// (cells x vector chunks x n_p^4 for the sum-factorised apply).
-template <int VB, int NT, int MINB, bool PACKED>
-cudaError_t launch_cell_multi(const CellJob* jobs, int n, cudaStream_t s) {
-  static_assert(sizeof(CellMultiArgs<PACKED>) <= 32764, "kernel parameter space");
-  if (n < 1 || n > GBC_MAX_SYS) return cudaErrorInvalidValue;
-  CellMultiArgs<PACKED> m;
-  m.ngroups = 0;
-  int k = 0;
-  double work[GBC_MAX_P - 1], wsum = 0;
-  size_t smem = 0;
-  for (int p = 2; p <= GBC_MAX_P; ++p) {
-    const gbc_ctx* c0 = nullptr;
-    long long item = 0;
-    const int s0 = k;
-    for (int i = 0; i < n; ++i) {
-      const gbc_ctx* c = jobs[i].c;
-      if (c->mesh.p != p) continue;
-      if (c->mesh.M >= (1LL << 29)) return cudaErrorInvalidValue;
-      if (!c0) {
-        c0 = c;
-      } else {
-        for (int d = 0; d < 3; ++d)
-          if (c->h[d] != c0->h[d] || c->k[d] != c0->k[d]) return cudaErrorInvalidValue;
-      }
-      fill_sys(m.sys[k], jobs[i], VB, item);
-      item += (long long)c->mesh.E * m.sys[k].vchunks;
-      ++k;
-    }
-    if (!c0 || item == 0) continue;
-    if (!fill_multi_tables<PACKED>(m, p, c0)) return cudaErrorInvalidValue;
-    CellGroup& G = m.grp[m.ngroups];
-    G.p = p;
-    G.kpt = (c0->k[0] != 0.0 || c0->k[1] != 0.0 || c0->k[2] != 0.0);
-    G.s0 = s0;
-    G.ns = k - s0;
-    G.nitems = item;
-    work[m.ngroups] = (double)item * std::pow((double)(p + 1), 4);
-    wsum += work[m.ngroups];
-    smem = std::max(smem, cell_smem_for_p<VB>(p));
-    ++m.ngroups;
-  }
-  for (int i = k; i < GBC_MAX_SYS; ++i) m.sys[i] = m.sys[0];
-  if (m.ngroups == 0) return cudaSuccess;
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  auto kern = hx_cell_multi_kernel<VB, NT, MINB, PACKED>;
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const long long total = (long long)nsm * per_sm;
-  long long blk = 0;
-  for (int g = 0; g < m.ngroups; ++g) {
-    CellGroup& G = m.grp[g];
-    long long nb = g + 1 == m.ngroups ? total - blk : (long long)std::llround(total * work[g] / wsum);
-    nb = std::max(1LL, std::min(nb, G.nitems));
-    G.blk0 = (int)blk;
-    G.nblk = (int)nb;
-    blk += nb;
-  }
-  kern<<<(unsigned)blk, NT, smem, s>>>(m);
-  return cudaGetLastError();
 }
 
 template <int VB, int NT, int MINB, bool PACKED>
