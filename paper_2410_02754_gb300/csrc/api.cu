@@ -186,12 +186,13 @@ gbc_status filter_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, int m, double lT,
       continue;
     }
     if (c->proj.natoms > 0) {
-      const size_t cb = sizeof(cplx<T>) * (size_t)c->proj.rows_total * nvec;
-      GBC_TRY(gbc_ensure_work(c, 2, 2 * cb));
+      size_t xoff = 0;
+      GBC_TRY(gbc_ensure_work(c, 2, nl_work_bytes(c, nvec, ldx, sizeof(cplx<T>), &xoff)));
       cplx<T>* C1 = (cplx<T>*)c->work[2];
       cplx<T>* C2 = C1 + (size_t)c->proj.rows_total * nvec;
+      void* bpre = xoff ? (char*)c->work[2] + xoff : nullptr;
       TimerScope ts(c, FAM_NONLOCAL, s);
-      GBC_CU(c, launch_nonlocal<T>(c, cur, Y, nvec, ldx, C1, C2, s, true));
+      GBC_CU(c, launch_nonlocal<T>(c, cur, Y, nvec, ldx, C1, C2, s, true, bpre));
     }
     {
       TimerScope ts(c, FAM_HX_LOCAL, s);

@@ -177,16 +177,17 @@ extern "C" gbc_status gbc_tune(gbc_ctx* c, int nvec, void* stream) {
   }
   // FP32 nonlocal engine: the SIMT kernels against the tcgen05 contractions
   if (c->proj.natoms > 0 && tc_nonlocal_supported(c->proj)) {
-    const size_t cb = sizeof(float2) * (size_t)c->proj.rows_total * nvec;
-    GBC_TRY(gbc_ensure_work(c, 2, 2 * cb));
+    size_t xoff = 0;
+    GBC_TRY(gbc_ensure_work(c, 2, nl_work_bytes(c, nvec, nvec, sizeof(float2), &xoff)));
     float2* C1 = (float2*)c->work[2];
     float2* C2 = C1 + (size_t)c->proj.rows_total * nvec;
+    void* bpre = xoff ? (char*)c->work[2] + xoff : nullptr;
     const int keep = c->nl_engine;
     float nlbest = 1e30f;
     for (int eng = 0; eng < 2; ++eng) {
       c->nl_engine = eng;
       const float ms = time_median(c, s, e0, e1, [&] {
-        return launch_nonlocal<float>(c, X, Y, nvec, nvec, C1, C2, s, true);
+        return launch_nonlocal<float>(c, X, Y, nvec, nvec, C1, C2, s, true, bpre);
       });
       ent.nl_ms[eng] = ms;
       if (ms >= 0.f && ms < nlbest) {
@@ -307,8 +308,11 @@ gbc_status record_filters(gbc_batch* b, std::vector<SysRun>& runs, cudaStream_t 
         if (r.c->proj.natoms == 0) continue;
         float2* C1 = (float2*)r.c->work[2];
         float2* C2 = C1 + (size_t)r.c->proj.rows_total * r.nvec;
+        size_t xoff = 0;
+        nl_work_bytes(r.c, r.nvec, r.ldx, sizeof(float2), &xoff);   // sized before the capture
+        void* bpre = xoff ? (char*)r.c->work[2] + xoff : nullptr;
         const cudaError_t e = launch_nonlocal<float>(r.c, (const float2*)cur_of(r), (float2*)r.Y,
-                                                     r.nvec, r.ldx, C1, C2, s, true);
+                                                     r.nvec, r.ldx, C1, C2, s, true, bpre);
         if (e != cudaSuccess) return bfail(b, GBC_ECUDA, std::string("nonlocal: ") + cudaGetErrorString(e));
         count += 3;
       }
@@ -497,7 +501,7 @@ gbc_status gbc_batch_filter(gbc_batch* b, void* const* X, const int* nvec, const
     const size_t bytes = el * 2 * (size_t)c->mesh.M * ldx[i];
     // every workspace the graph touches is allocated before capture
     if (gbc_ensure_work(c, 0, bytes) != GBC_OK || gbc_ensure_work(c, 1, bytes) != GBC_OK ||
-        gbc_ensure_work(c, 2, std::max<size_t>(64, 2 * el * (size_t)c->proj.rows_total * nvec[i])) != GBC_OK)
+        gbc_ensure_work(c, 2, nl_work_bytes(c, nvec[i], ldx[i], el, nullptr)) != GBC_OK)
       return bfail(b, GBC_ENOMEM, "system " + std::to_string(i) + ": " + c->err);
     SysRun& r = runs[i];
     r.c = c;

@@ -115,6 +115,8 @@ struct ProjDev {
   int4* d_tcexp_chunks = nullptr;    // (first owned index, count, slot offset, slot count)
   int* d_tcexp_slots = nullptr;      // atom of each slot
   int tc_max_slots = 0;              // largest slot count (> GBC_TC_MAX_SLOTS: no tensor path)
+  long long ntc_slots = 0;           // slot instances over all chunks
+  float* d_xA = nullptr;             // [ntc_slots] packed A blocks of the expansion (or null)
   // raw inputs kept on device for recomputation at a new k
   double* d_pvals = nullptr;
   int* d_entry_cell = nullptr;
@@ -251,13 +253,23 @@ void tcl_free(TclState* t);
 // support row, other rows untouched)
 template <typename T>
 cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx,
-                            cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s, bool overwrite = false);
+                            cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s, bool overwrite = false,
+                            void* bpre = nullptr);
+// nonlocal workspace for nvec vectors of element size el: C, C' and (FP32 tensor-core
+// expansion) its B blocks; *bpre_off = their offset, 0 when not used
+size_t nl_work_bytes(const gbc_ctx* c, int nvec, int ldx, size_t el, size_t* bpre_off);
 // tcgen05 projector contractions (nonlocal_tc.cu), FP32 only
 bool tc_nonlocal_supported(const ProjDev& pj);
 cudaError_t launch_tc_project(const ProjDev& pj, long long M, const float2* X, int nvec, int ldx,
                               float2* Cbuf, cudaStream_t s);
+// overwrite with bpre (tc_expand_bpre_bytes of device scratch, 256-byte aligned): the
+// expansion from packed operands; otherwise the operand-staging kernel
 cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, const float2* Cp,
-                             cudaStream_t s, bool overwrite = false);
+                             cudaStream_t s, bool overwrite = false, void* bpre = nullptr);
+// scratch bytes of the packed expansion's B blocks for an nvec-vector block (0: not used)
+size_t tc_expand_bpre_bytes(const ProjDev& pj, int nvec, int ldx);
+// pack the expansion's A blocks from the FP32 P tables (allocates them once per projector set)
+cudaError_t tc_expand_prepare(ProjDev& pj, cudaStream_t s);
 cudaError_t tc_nonlocal_reset(cudaStream_t s);
 cudaError_t tc_nonlocal_error(int* err, cudaStream_t s);
 

@@ -9,6 +9,7 @@
 //                         a plain read-modify-write of Y, no atomics)
 // P_a is the node-based projector table (one row per distinct free node of the
 // support, so nodes shared by several support cells are stored once).
+#include <algorithm>
 #include <type_traits>
 
 #include "gbc_internal.h"
@@ -187,7 +188,8 @@ bool use_tc(const gbc_ctx* c) { return c->nl_engine == GBC_NL_TENSOR && tc_nonlo
 
 template <typename T>
 cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx,
-                            cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s, bool overwrite) {
+                            cplx<T>* Cbuf, cplx<T>* Cpbuf, cudaStream_t s, bool overwrite,
+                            void* bpre) {
   const ProjDev& pj = c->proj;
   if (pj.natoms == 0 || nvec == 0 || pj.nchunks == 0 || pj.nexp_chunks == 0) return cudaSuccess;
   cudaError_t e = launch_nl_project<T>(c, X, nvec, ldx, Cbuf, s);
@@ -200,7 +202,7 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if constexpr (std::is_same<T, float>::value) {
-    if (use_tc(c)) return launch_tc_expand(pj, Y, nvec, ldx, Cpbuf, s, overwrite);
+    if (use_tc(c)) return launch_tc_expand(pj, Y, nvec, ldx, Cpbuf, s, overwrite, bpre);
   }
   const cplx<T>* P = std::is_same<T, double>::value ? (const cplx<T>*)pj.d_P64
                                                     : (const cplx<T>*)pj.d_P32;
@@ -240,6 +242,14 @@ template cudaError_t launch_nl_project<double>(gbc_ctx*, const double2*, int, in
                                                cudaStream_t);
 
 template cudaError_t launch_nonlocal<float>(gbc_ctx*, const float2*, float2*, int, int, float2*,
-                                            float2*, cudaStream_t, bool);
+                                            float2*, cudaStream_t, bool, void*);
 template cudaError_t launch_nonlocal<double>(gbc_ctx*, const double2*, double2*, int, int,
-                                             double2*, double2*, cudaStream_t, bool);
+                                             double2*, double2*, cudaStream_t, bool, void*);
+
+size_t nl_work_bytes(const gbc_ctx* c, int nvec, int ldx, size_t el, size_t* bpre_off) {
+  const size_t cb = el * (size_t)c->proj.rows_total * (size_t)nvec;
+  const size_t off = (2 * cb + 255) & ~(size_t)255;
+  const size_t xb = el == sizeof(float2) ? tc_expand_bpre_bytes(c->proj, nvec, ldx) : 0;
+  if (bpre_off) *bpre_off = xb ? off : 0;
+  return std::max<size_t>(64, xb ? off + xb : 2 * cb);
+}

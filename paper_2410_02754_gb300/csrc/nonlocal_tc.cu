@@ -149,7 +149,8 @@ k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __rest
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Ns + kPrjChunk);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
-  if (*reinterpret_cast<volatile int*>(&g_nltc_err)) return;   // an earlier CTA gave up
+  // an earlier CTA gave up (read once, the same decision in every thread)
+  if (__syncthreads_or(*reinterpret_cast<volatile int*>(&g_nltc_err))) return;
   const int4 ch = chunks[chunk0 + blockIdx.y];   // (atom, first position, count, node offset)
   const int atom = ch.x, j0 = ch.y, cnt = min(ch.z, kPrjChunk), noff = ch.w;
   const int npj = atom_npj[atom];
@@ -336,7 +337,8 @@ k_tc_project_tma(const __grid_constant__ CUtensorMap xmap, int ldx, int nvec,
   auto segdone = [&](int p) { return tc::smem_u32(bars + 2 * kStages + 2 * kAB + p); };
   auto setfree = [&](int p) { return tc::smem_u32(bars + 2 * kStages + 2 * kAB + 2 + p); };
 
-  if (*reinterpret_cast<volatile int*>(&g_nltc_err)) return;   // an earlier CTA gave up
+  // an earlier CTA gave up (read once, the same decision in every thread)
+  if (__syncthreads_or(*reinterpret_cast<volatile int*>(&g_nltc_err))) return;
   const int4 ch = chunks[chunk0 + blockIdx.y];   // (atom, first position, count, node offset)
   const int atom = ch.x, j0 = ch.y, cnt = min(ch.z, kPrjChunk), noff = ch.w;
   const int npj = atom_npj[atom];
@@ -549,7 +551,8 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
   uint64_t* mbar = reinterpret_cast<uint64_t*>(s_node + 128);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
-  if (*reinterpret_cast<volatile int*>(&g_nltc_err)) return;   // an earlier CTA gave up
+  // an earlier CTA gave up (read once, the same decision in every thread)
+  if (__syncthreads_or(*reinterpret_cast<volatile int*>(&g_nltc_err))) return;
   const int4 ch = chunks[chunk0 + blockIdx.y];   // (first owned index, count, slot offset, slots)
   const int u0 = ch.x, cnt = min(ch.y, 128), nsl = min(ch.w, GBC_TC_MAX_SLOTS);
   const int tid = threadIdx.x;
@@ -677,6 +680,269 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
   tc_end<128>(t);
 }
 
+// ---- expansion from packed operands -----------------------------------------------
+// The same product D = A B^T per (chunk, column tile) with both operands prepared
+// ahead in the MMA's shared-memory layout, so the kernel only copies, multiplies and
+// stores:
+//   A (P values): per slot instance of a chunk (setup, k_xpack_a), K = 40 (2 n_pj <= 40
+//       zero-padded), 128 rows; rows of nodes outside the slot atom's support are zero.
+//   B (C' values): per (atom, column tile) after the coupling step (k_xpack_b).
+// Each operand of one slot is [hi: 5 K steps][lo: 5 K steps], a K step being 128 rows
+// x 8 values in the 32-byte swizzled layout (4 KB): 40 KB, one bulk copy.
+constexpr int kXSteps = 5;                        // K steps of 8 per slot
+constexpr int kXK = 8 * kXSteps;                  // K per slot (>= 2 n_pj)
+constexpr uint32_t kXBlk = 128u * 32u;            // one K step, bytes
+constexpr uint32_t kXHalf = kXSteps * kXBlk;      // hi or lo part of one operand
+constexpr uint32_t kXOp = 2 * kXHalf;             // one operand (40 KB)
+constexpr uint32_t kXStage = 2 * kXOp;            // A and B of one slot (80 KB)
+constexpr int kXRow = 64 * 4 + 16;                // epilogue row: half a tile + pad, bytes
+constexpr int kXThreads = 192;                    // producer, MMA, 4 epilogue warps
+
+constexpr size_t xexp_smem() { return 1024 + 2 * (size_t)kXStage + 128 * (size_t)kXRow + 256; }
+
+// store the hi / lo split of K values v[0..kXK) of row r into an operand block
+__device__ __forceinline__ void xpack_row(float* blk, int r, const float (&v)[kXK]) {
+#pragma unroll
+  for (int ks = 0; ks < kXSteps; ++ks) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float hi[4], lo[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) tc::split_tf32(v[8 * ks + 4 * h + e], hi[e], lo[e]);
+      const int off = ks * 1024 + tc::sw32(r, h);
+      *reinterpret_cast<float4*>(blk + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<float4*>(blk + kXHalf / 4 + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    }
+  }
+}
+
+// A blocks: one CTA per chunk, thread r = row (owned node u0 + r); slot sl of the
+// chunk at block (slot offset + sl).  A[r][2chi] = Re P_b(node, chi), [2chi+1] = Im.
+__global__ void __launch_bounds__(128)
+k_xpack_a(float* __restrict__ Apre, const int4* __restrict__ chunks, const int* __restrict__ slots,
+          const int* __restrict__ own_pos, const int* __restrict__ own_xptr,
+          const int2* __restrict__ own_xinc, const float2* __restrict__ P,
+          const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off) {
+  const int4 ch = chunks[blockIdx.x];
+  const int r = threadIdx.x;
+  const int u = ch.x + r;
+  for (int sl = 0; sl < ch.w; ++sl) {
+    const int b = slots[ch.z + sl];
+    int pos = -1;
+    if (r < ch.y) {
+      if (sl == 0) {
+        pos = own_pos[u];
+      } else {
+        for (int k = own_xptr[u]; k < own_xptr[u + 1]; ++k)
+          if (own_xinc[k].x == b) pos = own_xinc[k].y;
+      }
+    }
+    const int npj = atom_npj[b];
+    float v[kXK];
+#pragma unroll
+    for (int k = 0; k < kXK; k += 2) {
+      float2 p = make_float2(0.f, 0.f);
+      if (pos >= 0 && k / 2 < npj) p = P[atom_pv_off[b] + (size_t)pos * npj + k / 2];
+      v[k] = p.x;
+      v[k + 1] = p.y;
+    }
+    xpack_row(Apre + (size_t)(ch.z + sl) * (kXOp / 4), r, v);
+  }
+}
+
+// B blocks: one CTA per (atom b, column tile j), thread n = real column 128 j + n of
+// the [2][ldx] complex node row.  B[re col][2chi] = Re C', [2chi+1] = -Im C';
+// B[im col][2chi] = Im C', [2chi+1] = Re C' (so D = Re / Im of sum_chi P C').
+__global__ void __launch_bounds__(128)
+k_xpack_b(float* __restrict__ Bpre, const float2* __restrict__ Cp, int ldx, int nvec,
+          const int* __restrict__ atom_npj, const int* __restrict__ atom_c_off) {
+  const int b = blockIdx.x, j = blockIdx.y, n = threadIdx.x;
+  const int col = j * 128 + n;
+  const int ci = col >> 1, s = ci / ldx, v = ci % ldx;
+  const bool ok = col < 4 * ldx && v < nvec;
+  const bool im = (col & 1) != 0;
+  const int npj = atom_npj[b], r0 = atom_c_off[b];
+  float x[kXK];
+#pragma unroll
+  for (int k = 0; k < kXK; k += 2) {
+    float2 c = make_float2(0.f, 0.f);
+    if (ok && k / 2 < npj) c = Cp[(size_t)(r0 + k + s) * nvec + v];
+    x[k] = im ? c.y : c.x;
+    x[k + 1] = im ? c.x : -c.y;
+  }
+  xpack_row(Bpre + ((size_t)b * gridDim.y + j) * (kXOp / 4), n, x);
+}
+
+// single-thread bounded wait that also gives up once another role has flagged a failure
+__device__ __forceinline__ bool wait_one(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    if (tc::mbar_try_wait(mbar, parity)) return true;
+    if ((i & 255u) == 255u && *abort_flag) break;
+  }
+  *abort_flag = 1;
+  atomicExch(&g_nltc_err, 1);
+  return false;
+}
+
+// Y rows of the owned nodes = P C' (overwrite), persistent over work items
+// (chunk, column tile), chunk-major, item = blockIdx.x + i gridDim.x:
+//   warp 0    one thread: bulk copies of each slot's A and B blocks into a two-stage ring
+//   warp 1    TMEM owner; one thread issues 5 K steps x 3 products (3xTF32) per slot
+//             into one of two 128-column accumulators
+//   warps 2-5 epilogue: TMEM -> registers -> the thread's own staging row -> bulk copy
+//             of 256 contiguous bytes of its node row; lane quadrant = warp % 4
+__global__ void __launch_bounds__(kXThreads, 1)
+k_tc_expand_ws(float* __restrict__ Yr, int ncols, int ntiles, long long nitems,
+               const int4* __restrict__ chunks, const int* __restrict__ slots,
+               const long long* __restrict__ own_node, const float* __restrict__ Apre,
+               const float* __restrict__ Bpre) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
+  unsigned char* stage0 = reinterpret_cast<unsigned char*>(base);
+  unsigned char* rows = stage0 + 2 * kXStage;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rows + 128 * kXRow);   // full[2] empty[2] tfull[2] tempty[2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  int* prog = reinterpret_cast<int*>(tslot + 2);   // [0] stage uses issued, [1] consumed, [2] commits
+  auto full = [&](int s) { return tc::smem_u32(bars + s); };
+  auto empty = [&](int s) { return tc::smem_u32(bars + 2 + s); };
+  auto tfull = [&](int a) { return tc::smem_u32(bars + 4 + a); };
+  auto tempty = [&](int a) { return tc::smem_u32(bars + 6 + a); };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // an earlier CTA gave up (read once, the same decision in every thread)
+  if (__syncthreads_or(*reinterpret_cast<volatile int*>(&g_nltc_err))) return;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 6; ++i) tc::mbar_init(tc::smem_u32(bars + i), 1);
+    for (int i = 6; i < 8; ++i) tc::mbar_init(tc::smem_u32(bars + i), 4);   // one per epilogue warp
+    *abort_flag = 0;
+    prog[0] = prog[1] = prog[2] = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tc::smem_u32(tslot), 256);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int use = 0;
+      for (long long it = blockIdx.x; it < nitems && !*abort_flag; it += gridDim.x) {
+        const int chn = (int)(it / ntiles), j = (int)(it % ntiles);
+        const int4 ch = chunks[chn];
+        bool ok = true;
+        for (int sl = 0; sl < ch.w; ++sl, ++use) {
+          const int st = use & 1;
+          if (use >= 2 && !wait_one(empty(st), ((use >> 1) - 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t dst = tc::smem_u32(stage0 + st * kXStage);
+          tc::mbar_arrive_expect_tx(full(st), kXStage);
+          tc::bulk_g2s(dst, Apre + (size_t)(ch.z + sl) * (kXOp / 4), kXOp, full(st));
+          tc::bulk_g2s(dst + kXOp, Bpre + ((size_t)slots[ch.z + sl] * ntiles + j) * (kXOp / 4), kXOp,
+                       full(st));
+          prog[0] = use + 1;
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_tf32(128, 128);
+      int use = 0, n = 0;
+      for (long long it = blockIdx.x; it < nitems && !*abort_flag; it += gridDim.x, ++n) {
+        const int acc = n & 1;
+        if (n >= 2 && !wait_one(tempty(acc), ((n >> 1) - 1) & 1, abort_flag)) break;
+        tc::fence_after_sync();
+        const int4 ch = chunks[(int)(it / ntiles)];
+        const uint32_t d = tmem + (uint32_t)(128 * acc);
+        bool ok = true;
+        for (int sl = 0; sl < ch.w; ++sl, ++use) {
+          const int st = use & 1;
+          if (!wait_one(full(st), (use >> 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          prog[1] = use + 1;
+          tc::fence_after_sync();
+          const uint32_t a = tc::smem_u32(stage0 + st * kXStage), b = a + kXOp;
+#pragma unroll
+          for (int ks = 0; ks < kXSteps; ++ks) {
+            const uint32_t o = ks * kXBlk;
+            tc::mma_tf32(d, tc::sdesc_sw32(a + o), tc::sdesc_sw32(b + o), idesc,
+                         (sl > 0 || ks > 0) ? 1u : 0u);
+            tc::mma_tf32(d, tc::sdesc_sw32(a + o), tc::sdesc_sw32(b + kXHalf + o), idesc, 1u);
+            tc::mma_tf32(d, tc::sdesc_sw32(a + kXHalf + o), tc::sdesc_sw32(b + o), idesc, 1u);
+          }
+          tc::mma_commit(empty(st));   // the stage is free once these MMAs complete
+        }
+        if (!ok) break;
+        tc::mma_commit(tfull(acc));
+        prog[2] = n + 1;
+      }
+    }
+  } else {
+    // epilogue: thread -> row r of the accumulator (TMEM lane r)
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    unsigned char* myrow = rows + r * kXRow;
+    const uint32_t myrow_s = tc::smem_u32(myrow);
+    int n = 0;
+    for (long long it = blockIdx.x; it < nitems; it += gridDim.x, ++n) {
+      const int acc = n & 1;
+      if (!wait_uniform(tfull(acc), (n >> 1) & 1, abort_flag)) break;
+      tc::fence_after_sync();
+      const int chn = (int)(it / ntiles), j = (int)(it % ntiles);
+      const int4 ch = chunks[chn];
+      const long long node = r < ch.y ? own_node[ch.x + r] : -1;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        float v[64];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float t[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * acc + 64 * h + 16 * c), t);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[16 * c + e] = t[e];
+        }
+        if (h == 1) {   // accumulator read: hand it back to the MMA thread
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(tempty(acc));
+        }
+        const int col0 = 128 * j + 64 * h;
+        const int nb = min(64, ncols - col0);
+        if (node >= 0 && nb > 0) {
+          tc::bulk_wait_read0();   // the previous copy out of this row has read it
+          float4* dst = reinterpret_cast<float4*>(myrow);
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+          tc::fence_proxy_async();
+          tc::bulk_s2g(Yr + node * (long long)ncols + col0, myrow_s, (uint32_t)nb * 4u);
+          tc::bulk_commit();
+        }
+      }
+    }
+    tc::bulk_wait0();
+  }
+  // ---- teardown: after an expired wait, bounded waits for the copies and MMAs
+  // still in flight before the TMEM is freed and the CTA exits
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) {
+    for (int u = prog[1]; u < prog[0]; ++u) tc::mbar_wait_bounded(full(u & 1), (u >> 1) & 1);
+    if (prog[1] > 0) tc::mbar_wait_bounded(empty((prog[1] - 1) & 1), ((prog[1] - 1) >> 1) & 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, 256);
+}
+
 template <int NB>
 cudaError_t run_tc_project(const ProjDev& pj, const float2* X, int nvec, int ldx, float2* Cbuf,
                            cudaStream_t s) {
@@ -779,8 +1045,43 @@ cudaError_t launch_tc_project(const ProjDev& pj, long long M, const float2* X, i
   }
 }
 
+size_t tc_expand_bpre_bytes(const ProjDev& pj, int nvec, int ldx) {
+  if (!pj.d_xA || ldx != nvec || nvec <= 0) return 0;
+  const size_t ntiles = (size_t)(4 * ldx + 127) / 128;
+  return (size_t)pj.natoms * ntiles * kXOp;
+}
+
+cudaError_t tc_expand_prepare(ProjDev& pj, cudaStream_t s) {
+  if (!tc_nonlocal_supported(pj) || 2 * pj.max_npj > kXK || pj.ntc_slots <= 0) return cudaSuccess;
+  if (!pj.d_xA && cudaMalloc(&pj.d_xA, (size_t)pj.ntc_slots * kXOp) != cudaSuccess) {
+    cudaGetLastError();   // no room: the expansion keeps staging its operands itself
+    pj.d_xA = nullptr;
+    return cudaSuccess;
+  }
+  k_xpack_a<<<(unsigned)pj.ntc_exp, 128, 0, s>>>(pj.d_xA, pj.d_tcexp_chunks, pj.d_tcexp_slots,
+                                                 pj.d_own_pos, pj.d_own_xptr, pj.d_own_xinc,
+                                                 pj.d_P32, pj.d_atom_npj, pj.d_atom_pv_off);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, const float2* Cp,
-                             cudaStream_t s, bool overwrite) {
+                             cudaStream_t s, bool overwrite, void* bpre) {
+  if (overwrite && bpre && tc_expand_bpre_bytes(pj, nvec, ldx) > 0) {
+    const int ntiles = (4 * ldx + 127) / 128;
+    k_xpack_b<<<dim3((unsigned)pj.natoms, (unsigned)ntiles), 128, 0, s>>>(
+        reinterpret_cast<float*>(bpre), Cp, ldx, nvec, pj.d_atom_npj, pj.d_atom_c_off);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    constexpr size_t smem = xexp_smem();
+    e = cudaFuncSetAttribute(k_tc_expand_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long nitems = (long long)pj.ntc_exp * ntiles;
+    const unsigned grid = (unsigned)std::min<long long>(nitems, gbc_sm_count());
+    k_tc_expand_ws<<<grid, kXThreads, smem, s>>>(reinterpret_cast<float*>(Y), 4 * ldx, ntiles, nitems,
+                                                 pj.d_tcexp_chunks, pj.d_tcexp_slots, pj.d_own_node,
+                                                 pj.d_xA, reinterpret_cast<const float*>(bpre));
+    return cudaGetLastError();
+  }
   constexpr size_t smem = expand_smem();
   cudaError_t e =
       cudaFuncSetAttribute(k_tc_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -387,6 +387,7 @@ gbc_status setup_projectors(gbc_ctx* c) {
   GBC_CU(c, cudaGetLastError());
   k_to_f32<<<(unsigned)((ntab + 2 + 255) / 256), 256>>>(pj.d_P64, pj.d_P32, ntab + 2);
   GBC_CU(c, cudaGetLastError());
+  GBC_CU(c, tc_expand_prepare(pj, 0));
   GBC_CU(c, cudaDeviceSynchronize());
   cudaFree(dbase);
   return GBC_OK;
@@ -495,6 +496,35 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
     own_extra[owner].push_back(ex);
     i = j;
   }
+  // within an owner, nodes held by the same further atoms are made adjacent (then
+  // ascending): the expansion chunks below then carry few atoms each, and the
+  // tensor-core expansion's K (2 n_pj per atom of a chunk) holds few zero rows
+  for (int a = 0; a < natoms; ++a) {
+    const size_t n = own_node[a].size();
+    std::vector<size_t> perm(n);
+    for (size_t j = 0; j < n; ++j) perm[j] = j;
+    auto& ex = own_extra[a];
+    auto& nd = own_node[a];
+    std::sort(perm.begin(), perm.end(), [&](size_t x, size_t y) {
+      const auto& ex_x = ex[x];
+      const auto& ex_y = ex[y];
+      if (ex_x.size() != ex_y.size()) return ex_x.size() < ex_y.size();
+      for (size_t k = 0; k < ex_x.size(); ++k)
+        if (ex_x[k].x != ex_y[k].x) return ex_x[k].x < ex_y[k].x;
+      return nd[x] < nd[y];
+    });
+    std::vector<long long> n2(n);
+    std::vector<int> p2(n);
+    std::vector<std::vector<int2>> e2(n);
+    for (size_t j = 0; j < n; ++j) {
+      n2[j] = nd[perm[j]];
+      p2[j] = own_pos[a][perm[j]];
+      e2[j] = std::move(ex[perm[j]]);
+    }
+    nd.swap(n2);
+    own_pos[a].swap(p2);
+    ex.swap(e2);
+  }
   std::vector<long long> onode;
   std::vector<int> opos, oxptr;
   std::vector<int2> oxinc;
@@ -575,6 +605,7 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
   GBC_TRY(upload(c, (void**)&pj.d_own_xinc, oxinc.data(), sizeof(int2) * oxinc.size()));
   GBC_TRY(upload(c, (void**)&pj.d_exp_chunks, echunks.data(), sizeof(int4) * echunks.size()));
   pj.ntc_exp = (int)tcchunks.size();
+  pj.ntc_slots = (long long)tcslots.size();
   pj.tc_max_slots = 0;
   for (const int4& q : tcchunks) pj.tc_max_slots = std::max(pj.tc_max_slots, q.w);
   GBC_TRY(upload(c, (void**)&pj.d_tcexp_chunks, tcchunks.data(), sizeof(int4) * tcchunks.size()));
@@ -600,7 +631,8 @@ void free_projectors(ProjDev& pj) {
                   pj.d_atom_delta_off, pj.d_atom_c_off, pj.d_P64, pj.d_P32, pj.d_delta64,
                   pj.d_delta32, pj.d_chunks, pj.d_own_node, pj.d_own_pos, pj.d_own_xptr,
                   pj.d_own_xinc, pj.d_exp_chunks, pj.d_tcexp_chunks, pj.d_tcexp_slots,
-                  pj.d_pvals, pj.d_entry_cell, pj.d_entry_img, pj.d_entry_atom, pj.d_entry_pos};
+                  pj.d_pvals, pj.d_entry_cell, pj.d_entry_img, pj.d_entry_atom, pj.d_entry_pos,
+                  pj.d_xA};
   for (void* p : ptrs) cudaFree(p);
   pj = ProjDev();
 }

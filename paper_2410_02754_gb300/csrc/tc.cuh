@@ -31,6 +31,22 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// 32-byte swizzle: a K step of R rows x 8 FP32 values is R rows of 32 bytes, 8 rows
+// form a 256-byte swizzle atom, and the 16-byte half c of row r sits at half
+// position c ^ ((r >> 2) & 1) (address bit 4 xor bit 7).  Offset in floats:
+__host__ __device__ __forceinline__ int sw32(int row, int half) {
+  return row * 8 + ((half ^ ((row >> 2) & 1)) << 2);
+}
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);   // start address >> 4
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(256 >> 4) << 32;          // stride byte offset: 8 rows x 32 B
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)6 << 61;                   // 32-byte swizzle
+  return d;
+}
+
 // instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M x N
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -129,6 +145,25 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
           dst),
       "l"(src), "r"(bytes), "r"(mbar)
       : "memory");
+}
+
+// bulk copy of ``bytes`` from shared to global memory (multiple of 16; both
+// addresses 16-byte aligned), tracked in this thread's bulk groups
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// this thread's committed bulk copies have read their shared-memory sources
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// ... and have completed
+__device__ __forceinline__ void bulk_wait0() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)

@@ -185,3 +185,42 @@ def test_expired_device_wait_is_reported_and_context_recovers(g):
     ctx.sync_status()
     assert rel(Yd.cpu().numpy().astype(np.complex128), ref) < 1e-5
     ctx.close()
+
+
+FILTER_CASES = [
+    # ncell, p, periodic, natoms, rc, channels, nvec  (ldx == nvec)
+    ((4, 4, 4), 3, (1, 1, 1), 6, 2.0, "spd", 48),      # two column tiles, the second half full
+    ((4, 4, 4), 3, (1, 1, 1), 6, 2.0, "spd", 37),      # last tile 20 real columns
+    ((6, 6, 6), 2, (1, 1, 1), 40, 0.8, "spd", 64),     # many atoms per expansion chunk
+    ((3, 2, 3), 4, (1, 0, 1), 3, 1.2, "s", 33),        # npj = 1, Dirichlet faces
+]
+
+
+@pytest.mark.parametrize("case", FILTER_CASES, ids=lambda c: f"{c[0]}-p{c[1]}-a{c[3]}-{c[5]}-n{c[6]}")
+def test_packed_expansion_filter_matches_oracle(g, case):
+    """The fused FP32 filter writes P C' into the accumulator with the expansion
+    from packed operands (ldx == nvec, tensor engine): a degree-3 filter against
+    the FP64 oracle's three-term recurrence and against the SIMT engine."""
+    from oracle import chfsi as oc
+    ncell, p, per, natoms, rc, ch, nvec = case
+    channels = syn.SPD_CHANNELS if ch == "spd" else ((0.5, 0),)
+    prob = syn.make_problem(ncell=ncell, h=(1.0, 1.0, 1.0), p=p, periodic=per,
+                            k=(0.1, -0.05, 0.2), natoms=natoms, rc=rc, seed=9, channels=channels)
+    d = fe.Discretisation(prob)
+    X = syn.random_block(d.mesh.nnodes, nvec, 17)
+    bounds = (1.0, 80.0, -2.0)
+    ref = oc.cheb_filter(d.apply_htilde, X, 3, *bounds)
+    out = {}
+    for engine in (0, 1):
+        ctx = g.Context(0)
+        ctx.set_problem(prob)
+        ctx.set_precision(1)
+        ctx.set_nonlocal_engine(engine)
+        assert ctx.nonlocal_engine() == engine
+        Xd = torch.from_numpy(X).to(torch.complex64).cuda()
+        ctx.filter(Xd, 3, *bounds)
+        ctx.sync_status()
+        out[engine] = Xd.cpu().numpy().astype(np.complex128)
+        ctx.close()
+        assert rel(out[engine], ref) < 2e-5, (engine, rel(out[engine], ref))
+    assert rel(out[1], out[0]) < 1e-5
