@@ -178,22 +178,24 @@ def hbm_peak():
         return 6800.0, "of fallback (6.8 TB/s)"
 
 
-def CELL_TRAFFIC(nvec):
+def CELL_TRAFFIC(nvec, variant):
     """DRAM bytes of one fused-recurrence cell-apply launch at ``nvec`` vectors on the
-    cube16_p6 mesh, scaled from the ncu capture at 32 vectors (profiles/), or None."""
-    per32 = CELL_TRAFFIC_32
+    cube16_p6 mesh, scaled from the ncu capture of the same variant at 32 vectors
+    (profiles/), or None."""
+    per32 = CELL_TRAFFIC_32.get(variant)
     if per32 is None:
-        return None, "no ncu capture of this kernel version"
+        return None, f"no ncu capture of variant {variant} of this kernel version"
     return (0.034e9 + (per32 - 0.034e9) * nvec / 32,
-            "ncu capture at 32 vectors (recurrence mode) scaled by vectors: 1.16x the "
-            "algorithmic bytes (X gather, interior Y / X_{k-1} reads and X_{k+1} writes, face-row "
-            "Y read-modify-write)")
+            f"ncu capture of variant {variant} at 32 vectors (recurrence mode) scaled by "
+            f"vectors: {per32 / 1.654e9:.2f}x the algorithmic bytes (X gather, interior Y / "
+            "X_{k-1} reads and X_{k+1} writes, face-row Y read-modify-write)")
 
 
 # DRAM bytes (read + write) of one recurrence-mode cell-apply launch on the cube16_p6 mesh at
-# 32 vectors, from the ncu capture in profiles/hx_cell_fused_cube16_p6_nvec32.md; 34 MB of it
-# are the fields (fixed), the rest grows with the vector count
-CELL_TRAFFIC_32 = 1.925e9
+# 32 vectors, per cell-apply variant, from the ncu capture in
+# profiles/hx_cell_fused_cube16_p6_nvec32.md; 34 MB of it are the fields (fixed), the rest
+# grows with the vector count
+CELL_TRAFFIC_32 = {2: 1.781e9}
 
 
 def tc_cell_leg(g, prob, k, X, nvec, peaks, simt_ms):
@@ -362,7 +364,7 @@ def run_gpu(args):
     var, vb, nt = ctx32[0].cell_variant()
     traffic, traffic_note = None, "no ncu capture of this kernel version"
     if args.config == "cube16_p6":
-        traffic, traffic_note = CELL_TRAFFIC(nvec)
+        traffic, traffic_note = CELL_TRAFFIC(nvec, var)
     roofline = {"bound": "alu",
                 "kernel": f"hx_cell_kernel<7,8,k!=0,VB={vb},NT={nt}> variant {var} (even-odd sum "
                           "factorisation, recurrence fused for cell-interior nodes)",
@@ -647,6 +649,28 @@ def run_gpu(args):
             "lowest_ritz_ha": [float(x) for x in ritz["fp64"][:4]]}
         c64.close()
 
+    # ---- slab40_p6 (the semi-periodic slab, 6.85M nodes, 640 atoms): one 32-vector block
+    # at degree 30 in FP32 and in FP64 from the same seeded block, and the Ritz-value
+    # difference after one filter + CholGS + RR (the full 256-vector block: --config slab40_p6)
+    if not args.no_slab and rank == 0:
+        try:
+            torch.cuda.empty_cache()
+            r = slab_measure(g, syn, torch.cuda.current_device(), 32, syn.CONFIGS["slab40_p6"]["degree"],
+                             3, 1)
+            out["slab"] = {
+                "value": r["units"] / (r["ms32"] / 1e3), "unit": UNIT, "ms_per_filter": r["ms32"],
+                "fp64": {"value": r["units"] / (r["ms64"] / 1e3), "ms_per_filter": r["ms64"],
+                         "mixed_over_fp64": r["ms64"] / r["ms32"]},
+                "ritz_maxdiff_vs_fp64_ha_lower_half": r["ritz_maxdiff_vs_fp64_ha_lower_half"],
+                "target_ha": 1e-6, "nonlocal_engine": r["engine"], "clocks": r["clocks"],
+                "how": f"40x40x20 cells, p = 6 ({r['nodes']:,} nodes), periodic x/y, Dirichlet z, "
+                       "640 atoms x 18 SOC projectors, one 32-vector block, degree "
+                       f"{syn.CONFIGS['slab40_p6']['degree']}, Gamma; FP32 = median of 3 filters "
+                       "after 1 warm-up, FP64 = one filter; cycle 0 (CholGS + RR) before, "
+                       "CholGS + RR after, lower half of the block"}
+        except Exception as exc:   # an auxiliary leg must not cost the headline line
+            out["slab"] = {"error": f"{type(exc).__name__}: {exc}"}
+
     # ---- CPU baseline: the oracle as it stands, bounded sample (rank 0, N = 1)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_sample(args, prob, ks[0], budget_s=args.cpu_budget)
@@ -837,32 +861,21 @@ def run_backward(args):
         print(json.dumps(out), flush=True)
 
 
-def run_slab(args):
-    """slab40_p6: the 40x40x20-cell semi-periodic slab (6,854,400 nodes, 640 atoms), measured
-    as the per-block filter throughput of one 256-vector block at degree 30 (the 20,000 states
-    are 79 such blocks, which do not fit the GPU together), FP32 against FP64 on the same
-    block: cycle 0 (CholGS + Rayleigh-Ritz), then timed filters, then CholGS + Rayleigh-Ritz
-    and the Ritz-value difference of the lower half.  The block is drawn on the device from
-    a seeded generator (uniform [-1, 1) parts), once per precision from the same seed."""
+def slab_measure(g, syn, local, nvec, degree, steps, warmup):
+    """The slab40_p6 mesh and atoms (40x40x20 cells, p = 6, 6,854,400 nodes, 640 atoms): one
+    block of ``nvec`` vectors filtered to ``degree`` in FP32 and in FP64 from the same seeded
+    block: cycle 0 (CholGS + Rayleigh-Ritz), the timed filters (FP32: median of ``steps``
+    after ``warmup``; FP64: one), then CholGS + Rayleigh-Ritz and the Ritz-value difference
+    of the lower half.  The block is drawn on the device from a seeded generator (uniform
+    [-1, 1) parts), once per precision from the same seed."""
     import numpy as np
     import torch
 
-    import __graft_entry__ as ge
-    import synthetic as syn
-    import paper_2410_02754_gb300 as g
-
-    rank, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "gloo")
-    _, _, local = dist_env()
-    torch.cuda.set_device(local)
-    ge.build()
     cfg = syn.CONFIGS["slab40_p6"]
-    nvec = args.nvec or cfg["nvec"]
-    degree = args.degree or cfg["degree"]
     prob = syn.config("slab40_p6", seed=0)
     M = prob.nnodes
     v0 = torch.from_numpy(syn.random_start(M, 0)).cuda()
     stream = torch.cuda.current_stream()
-
     def block(dtype):
         gen = torch.Generator(device="cuda")
         gen.manual_seed(1234)
@@ -876,6 +889,8 @@ def run_slab(args):
         c = g.Context(local)
         c.set_problem(prob)
         c.set_precision(prec)
+        if prec == g.FP32:
+            c.tune(nvec)
         lo, hi = c.lanczos_bounds(v0, cfg["lanczos"])
         X = block(dtype)
         c.cholgs(X)
@@ -884,7 +899,7 @@ def run_slab(args):
         # each timed filter starts from the cycle-0 block (restored outside the timed region);
         # with nrep = 1 the block is filtered in place (no second copy of a 56 GB FP64 block)
         Xw = X.clone() if nrep > 1 else X
-        for _ in range(args.warmup if nrep > 1 else 0):
+        for _ in range(warmup if nrep > 1 else 0):
             Xw.copy_(X)
             c.filter(Xw, degree, lT, hi, lmin)
         times = []
@@ -910,10 +925,36 @@ def run_slab(args):
         torch.cuda.empty_cache()
         return ms, np.asarray(r), clk.summary(), engine
 
-    ms32, r32, clocks, engine = run(g.FP32, torch.complex64, args.steps)
+    ms32, r32, clocks, engine = run(g.FP32, torch.complex64, steps)
     ms64, r64, _, _ = run(g.FP64, torch.complex128, 1)
     units = M * nvec * degree
     half = nvec // 2
+    return {"units": units, "nodes": M, "ms32": ms32, "ms64": ms64, "engine": engine,
+            "clocks": clocks,
+            "ritz_maxdiff_vs_fp64_ha_lower_half": float(np.abs(r32 - r64)[:half].max())}
+
+
+def run_slab(args):
+    """slab40_p6: the 40x40x20-cell semi-periodic slab (6,854,400 nodes, 640 atoms), measured
+    as the per-block filter throughput of one 256-vector block at degree 30 (the 20,000 states
+    are 79 such blocks, which do not fit the GPU together), FP32 against FP64 on the same
+    block (slab_measure)."""
+    import torch
+
+    import __graft_entry__ as ge
+    import synthetic as syn
+    import paper_2410_02754_gb300 as g
+
+    rank, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "gloo")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    ge.build()
+    cfg = syn.CONFIGS["slab40_p6"]
+    nvec = args.nvec or cfg["nvec"]
+    degree = args.degree or cfg["degree"]
+    r = slab_measure(g, syn, local, nvec, degree, args.steps, args.warmup)
+    M, units, ms32, ms64, engine, clocks = (r["nodes"], r["units"], r["ms32"], r["ms64"],
+                                            r["engine"], r["clocks"])
     out = {"metric": METRIC + " (slab, per 256-vector block)", "value": units / (ms32 / 1e3),
            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -925,7 +966,7 @@ def run_slab(args):
                       "l2": "inputs larger than L2 (28 GB FP32 block)"},
            "fp64": {"value": units / (ms64 / 1e3), "ms_per_filter": ms64,
                     "mixed_over_fp64": ms64 / ms32},
-           "accuracy": {"ritz_maxdiff_vs_fp64_ha_lower_half": float(np.abs(r32 - r64)[:half].max()),
+           "accuracy": {"ritz_maxdiff_vs_fp64_ha_lower_half": r["ritz_maxdiff_vs_fp64_ha_lower_half"],
                         "target_ha": 1e-6,
                         "how": "cycle 0, one filter, CholGS, Rayleigh-Ritz, from the same seeded "
                                "block in each precision; FP32 time = median of the timed "
@@ -1013,6 +1054,7 @@ def main():
     ap.add_argument("--no-twogrid", action="store_true")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core cell-apply leg")
     ap.add_argument("--no-batch16", action="store_true", help="skip the batch16 leg")
+    ap.add_argument("--no-slab", action="store_true", help="skip the slab40_p6 leg")
     ap.add_argument("--scf-steps", type=int, default=2, help="SCF steps of the scf leg (0: off)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

@@ -695,10 +695,11 @@ constexpr uint32_t kXBlk = 128u * 32u;            // one K step, bytes
 constexpr uint32_t kXHalf = kXSteps * kXBlk;      // hi or lo part of one operand
 constexpr uint32_t kXOp = 2 * kXHalf;             // one operand (40 KB)
 constexpr uint32_t kXStage = 2 * kXOp;            // A and B of one slot (80 KB)
-constexpr int kXRow = 64 * 4 + 16;                // epilogue row: half a tile + pad, bytes
+constexpr int kXRow = 128 * 4 + 16;               // epilogue row: one tile row + pad, bytes
 constexpr int kXThreads = 192;                    // producer, MMA, 4 epilogue warps
 
-constexpr size_t xexp_smem() { return 1024 + 2 * (size_t)kXStage + 128 * (size_t)kXRow + 256; }
+// 256-byte alignment (the 32-byte swizzle atom), two stages, 128 staging rows, barriers
+constexpr size_t xexp_smem() { return 256 + 2 * (size_t)kXStage + 128 * (size_t)kXRow + 128; }
 
 // store the hi / lo split of K values v[0..kXK) of row r into an operand block
 __device__ __forceinline__ void xpack_row(float* blk, int r, const float (&v)[kXK]) {
@@ -784,20 +785,22 @@ __device__ __forceinline__ bool wait_one(uint32_t mbar, uint32_t parity, volatil
   return false;
 }
 
-// Y rows of the owned nodes = P C' (overwrite), persistent over work items
-// (chunk, column tile), chunk-major, item = blockIdx.x + i gridDim.x:
-//   warp 0    one thread: bulk copies of each slot's A and B blocks into a two-stage ring
+// Y rows of the owned nodes = P C' (overwrite), persistent: CTA b takes the chunks
+// b, b + gridDim.x, ... and every column tile of each in turn:
+//   warp 0    one thread: bulk copies of each slot's A and B blocks into a two-stage ring;
+//             an A block already held by the stage (chunks of one or two atoms, from the
+//             previous tile) is not copied again
 //   warp 1    TMEM owner; one thread issues 5 K steps x 3 products (3xTF32) per slot
 //             into one of two 128-column accumulators
-//   warps 2-5 epilogue: TMEM -> registers -> the thread's own staging row -> bulk copy
-//             of 256 contiguous bytes of its node row; lane quadrant = warp % 4
+//   warps 2-5 epilogue: TMEM -> registers -> the thread's own staging row -> one bulk
+//             copy of the tile's 512 contiguous bytes of its node row; lane quadrant = warp % 4
 __global__ void __launch_bounds__(kXThreads, 1)
-k_tc_expand_ws(float* __restrict__ Yr, int ncols, int ntiles, long long nitems,
+k_tc_expand_ws(float* __restrict__ Yr, int ncols, int ntiles, int nchunks,
                const int4* __restrict__ chunks, const int* __restrict__ slots,
                const long long* __restrict__ own_node, const float* __restrict__ Apre,
                const float* __restrict__ Bpre) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 255) & ~(uintptr_t)255;
   unsigned char* stage0 = reinterpret_cast<unsigned char*>(base);
   unsigned char* rows = stage0 + 2 * kXStage;
   uint64_t* bars = reinterpret_cast<uint64_t*>(rows + 128 * kXRow);   // full[2] empty[2] tfull[2] tempty[2]
@@ -831,37 +834,45 @@ k_tc_expand_ws(float* __restrict__ Yr, int ncols, int ntiles, long long nitems,
   if (warp == 0) {
     if (lane == 0) {
       int use = 0;
-      for (long long it = blockIdx.x; it < nitems && !*abort_flag; it += gridDim.x) {
-        const int chn = (int)(it / ntiles), j = (int)(it % ntiles);
+      int held0 = -1, held1 = -1;   // slot instance whose A block each stage holds
+      bool ok = true;
+      for (int chn = blockIdx.x; chn < nchunks && ok && !*abort_flag; chn += gridDim.x) {
         const int4 ch = chunks[chn];
-        bool ok = true;
-        for (int sl = 0; sl < ch.w; ++sl, ++use) {
-          const int st = use & 1;
-          if (use >= 2 && !wait_one(empty(st), ((use >> 1) - 1) & 1, abort_flag)) {
-            ok = false;
-            break;
+        for (int j = 0; j < ntiles && ok; ++j) {
+          for (int sl = 0; sl < ch.w; ++sl, ++use) {
+            const int st = use & 1;
+            if (use >= 2 && !wait_one(empty(st), ((use >> 1) - 1) & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t dst = tc::smem_u32(stage0 + st * kXStage);
+            const bool loadA = (st ? held1 : held0) != ch.z + sl;
+            tc::mbar_arrive_expect_tx(full(st), loadA ? kXStage : kXOp);
+            if (loadA) tc::bulk_g2s(dst, Apre + (size_t)(ch.z + sl) * (kXOp / 4), kXOp, full(st));
+            tc::bulk_g2s(dst + kXOp, Bpre + ((size_t)slots[ch.z + sl] * ntiles + j) * (kXOp / 4),
+                         kXOp, full(st));
+            if (st) held1 = ch.z + sl;
+            else held0 = ch.z + sl;
+            prog[0] = use + 1;
           }
-          const uint32_t dst = tc::smem_u32(stage0 + st * kXStage);
-          tc::mbar_arrive_expect_tx(full(st), kXStage);
-          tc::bulk_g2s(dst, Apre + (size_t)(ch.z + sl) * (kXOp / 4), kXOp, full(st));
-          tc::bulk_g2s(dst + kXOp, Bpre + ((size_t)slots[ch.z + sl] * ntiles + j) * (kXOp / 4), kXOp,
-                       full(st));
-          prog[0] = use + 1;
         }
-        if (!ok) break;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_tf32(128, 128);
       int use = 0, n = 0;
-      for (long long it = blockIdx.x; it < nitems && !*abort_flag; it += gridDim.x, ++n) {
+      bool ok = true;
+      for (int chn = blockIdx.x; chn < nchunks && ok && !*abort_flag; chn += gridDim.x)
+      for (int j = 0; j < ntiles && ok; ++j, ++n) {
         const int acc = n & 1;
-        if (n >= 2 && !wait_one(tempty(acc), ((n >> 1) - 1) & 1, abort_flag)) break;
+        if (n >= 2 && !wait_one(tempty(acc), ((n >> 1) - 1) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
         tc::fence_after_sync();
-        const int4 ch = chunks[(int)(it / ntiles)];
+        const int4 ch = chunks[chn];
         const uint32_t d = tmem + (uint32_t)(128 * acc);
-        bool ok = true;
         for (int sl = 0; sl < ch.w; ++sl, ++use) {
           const int st = use & 1;
           if (!wait_one(full(st), (use >> 1) & 1, abort_flag)) {
@@ -893,36 +904,43 @@ k_tc_expand_ws(float* __restrict__ Yr, int ncols, int ntiles, long long nitems,
     unsigned char* myrow = rows + r * kXRow;
     const uint32_t myrow_s = tc::smem_u32(myrow);
     int n = 0;
-    for (long long it = blockIdx.x; it < nitems; it += gridDim.x, ++n) {
-      const int acc = n & 1;
-      if (!wait_uniform(tfull(acc), (n >> 1) & 1, abort_flag)) break;
-      tc::fence_after_sync();
-      const int chn = (int)(it / ntiles), j = (int)(it % ntiles);
+    bool ok = true;
+    for (int chn = blockIdx.x; chn < nchunks && ok; chn += gridDim.x) {
       const int4 ch = chunks[chn];
       const long long node = r < ch.y ? own_node[ch.x + r] : -1;
+      for (int j = 0; j < ntiles; ++j, ++n) {
+        const int acc = n & 1;
+        if (!wait_uniform(tfull(acc), (n >> 1) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const int col0 = 128 * j;
+        const int nb = min(128, ncols - col0);
+        if (node >= 0) tc::bulk_wait_read0();   // the previous copy out of this row has read it
+        float4* dst = reinterpret_cast<float4*>(myrow);
 #pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        float v[64];
+        for (int h = 0; h < 2; ++h) {
+          float v[64];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float t[16];
-          tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * acc + 64 * h + 16 * c), t);
+          for (int c = 0; c < 4; ++c) {
+            float t[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * acc + 64 * h + 16 * c), t);
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[16 * c + e] = t[e];
+            for (int e = 0; e < 16; ++e) v[16 * c + e] = t[e];
+          }
+          if (h == 1) {   // accumulator read: hand it back to the MMA thread
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tempty(acc));
+          }
+          if (node >= 0) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              dst[16 * h + e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+          }
         }
-        if (h == 1) {   // accumulator read: hand it back to the MMA thread
-          tc::fence_before_sync();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(tempty(acc));
-        }
-        const int col0 = 128 * j + 64 * h;
-        const int nb = min(64, ncols - col0);
-        if (node >= 0 && nb > 0) {
-          tc::bulk_wait_read0();   // the previous copy out of this row has read it
-          float4* dst = reinterpret_cast<float4*>(myrow);
-#pragma unroll
-          for (int e = 0; e < 16; ++e)
-            dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        if (node >= 0) {
           tc::fence_proxy_async();
           tc::bulk_s2g(Yr + node * (long long)ncols + col0, myrow_s, (uint32_t)nb * 4u);
           tc::bulk_commit();
@@ -1075,9 +1093,8 @@ cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, co
     constexpr size_t smem = xexp_smem();
     e = cudaFuncSetAttribute(k_tc_expand_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long long nitems = (long long)pj.ntc_exp * ntiles;
-    const unsigned grid = (unsigned)std::min<long long>(nitems, gbc_sm_count());
-    k_tc_expand_ws<<<grid, kXThreads, smem, s>>>(reinterpret_cast<float*>(Y), 4 * ldx, ntiles, nitems,
+    const unsigned grid = (unsigned)std::min(pj.ntc_exp, gbc_sm_count());
+    k_tc_expand_ws<<<grid, kXThreads, smem, s>>>(reinterpret_cast<float*>(Y), 4 * ldx, ntiles, pj.ntc_exp,
                                                  pj.d_tcexp_chunks, pj.d_tcexp_slots, pj.d_own_node,
                                                  pj.d_xA, reinterpret_cast<const float*>(bpre));
     return cudaGetLastError();
