@@ -46,7 +46,8 @@ typedef enum {
   GBC_ESTATE = 4,        /* call out of order (e.g. apply before set_mesh/set_fields)   */
   GBC_ENOTPD = 5,        /* Cholesky met a non-positive pivot (overlap not positive def.) */
   GBC_ETIMEOUT = 6,      /* an iteration cap was reached (eigensolver did not converge)  */
-  GBC_EUNSUPPORTED = 7   /* valid request this build does not implement (p, nq, npj)     */
+  GBC_EUNSUPPORTED = 7,  /* valid request this build does not implement (p, nq, npj)     */
+  GBC_ECHECK = 8         /* checked build: a device index check failed (gbc_last_error)  */
 } gbc_status;
 
 typedef enum {
@@ -126,8 +127,11 @@ gbc_status gbc_get_nonlocal_engine(const gbc_ctx* ctx, int* engine);
 
 /* Synchronise ``stream`` and report errors that kernels record on the device
  * instead of trapping: GBC_ETIMEOUT if a bounded wait of a tensor-core kernel
- * expired since the previous call (its results are then invalid), GBC_ECUDA
- * for a CUDA error, else GBC_OK.  Clears the recorded flag. */
+ * expired since the previous call (its results are then invalid); in the checked
+ * build, GBC_ECHECK if a kernel met a node or row index out of range (the first one,
+ * with its site, in gbc_last_error; the access was skipped, results are invalid);
+ * GBC_ECUDA for a CUDA error, else GBC_OK.  Clears the recorded flags (they are
+ * library-wide, not per context). */
 gbc_status gbc_sync_status(gbc_ctx* ctx, void* stream);
 
 /* Number M of free FE nodes (spinor DOFs per vector = 2M).  gbc_get_ndof is the
@@ -407,6 +411,20 @@ gbc_status gbc_tc_gemm_nt(const float* A, const float* B, float* D, int M, int N
  * next gbc_sync_status returns GBC_ETIMEOUT (and clears it) while the context
  * stays usable.  Synchronous; GBC_EINVAL for a cap out of range. */
 gbc_status gbc_tc_wait_selftest(int max_iter, void* stream);
+
+/* ---- checked build ---------------------------------------------------------------
+ * The same sources compiled with -DGBCHFSI_CHECKED give libgbchfsi_checked.so (the
+ * Python binding loads it when GBCHFSI_CHECKED=1): before each node or row index is used,
+ * the FP32 and FP64 cell applies, the face-row recurrence and the nonlocal kernels
+ * check it against the mesh; the first index out of range is recorded with its site and
+ * the access is skipped, and gbc_sync_status returns GBC_ECHECK.  No counterpart in the
+ * paper (a debugging aid).  *checked = 1 in the checked build, else 0. */
+gbc_status gbc_build_info(int* checked);
+/* Checked build: one guarded store at ``index`` into a 64-entry device array; an index
+ * outside [0, 64) is recorded (site 7) and skipped, so the next gbc_sync_status on any
+ * context returns GBC_ECHECK.  Synchronous.  Default build: the guard is compiled out,
+ * so an index outside [0, 64) returns GBC_EUNSUPPORTED without a launch. */
+gbc_status gbc_check_selftest(long long index, void* stream);
 
 /* ---- tracing -------------------------------------------------------------- */
 

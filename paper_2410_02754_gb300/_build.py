@@ -2,7 +2,10 @@
 
 Each translation unit is compiled in parallel, then linked into
 ``paper_2410_02754_gb300/libgbchfsi.so``.  Usage: ``python -m
-paper_2410_02754_gb300._build`` or ``build()`` from Python.
+paper_2410_02754_gb300._build`` or ``build()`` from Python.  ``build(checked=True)``
+(``--checked``) compiles the same sources with -DGBCHFSI_CHECKED into
+``libgbchfsi_checked.so``: device index checks in the hot kernels, reported through
+gbc_sync_status (a debugging build; the binding loads it when GBCHFSI_CHECKED=1).
 """
 from __future__ import annotations
 
@@ -18,6 +21,8 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libgbchfsi.so")
 BUILD = os.path.join(HERE, "_build")
+OUT_CHECKED = os.path.join(HERE, "libgbchfsi_checked.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC, "-I" + CSRC]
@@ -34,20 +39,22 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    out, bdir = (OUT_CHECKED, BUILD_CHECKED) if checked else (OUT, BUILD)
+    flags = FLAGS + (["-DGBCHFSI_CHECKED"] if checked else [])
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INC, "gbchfsi.h"))
-    if not force and os.path.exists(OUT):
-        t = os.path.getmtime(OUT)
+    if not force and os.path.exists(out):
+        t = os.path.getmtime(out)
         if all(os.path.getmtime(d) <= t for d in deps):
-            return OUT
-    os.makedirs(BUILD, exist_ok=True)
+            return out
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -57,14 +64,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = OUT + ".tmp"
+    tmp = out + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -107,11 +107,6 @@ TimerScope::~TimerScope() {
 
 namespace {
 
-size_t block_bytes(const gbc_ctx* c, int ldx) {
-  const size_t el = c->prec == GBC_FP64 ? sizeof(double2) : sizeof(float2);
-  return el * 2 * (size_t)c->mesh.M * (size_t)ldx;
-}
-
 gbc_status check_block(gbc_ctx* c, const void* X, int nvec, int ldx) {
   if (!X) return gbc_fail(c, GBC_EINVAL, "null block pointer");
   if (nvec < 0 || ldx < 1 || nvec > ldx) return gbc_fail(c, GBC_EINVAL, "need 0 <= nvec <= ldx, ldx >= 1");
@@ -200,7 +195,7 @@ gbc_status filter_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, int m, double lT,
       GBC_CU(c, launch_cell_f32(&j, 1, c->cell_var, s));
     }
     TimerScope ts(c, FAM_CHEB, s);
-    GBC_CU(c, launch_cheb_rows<T>(Y, cur, prev, out, invmd, c->d_face_rows, c->nface, nvec, ldx,
+    GBC_CU(c, launch_cheb_rows<T>(Y, cur, prev, out, invmd, c->d_face_rows, c->nface, c->mesh.M, nvec, ldx,
                                   a, cc, b, s));
   }
   if (m & 1) GBC_CU(c, launch_copy_block<T>(W, X, c->mesh.M, nvec, ldx, s));
@@ -424,6 +419,14 @@ gbc_status gbc_apply_h_dev(gbc_ctx* c, const void* X, void* Y, int nvec, int ldx
 // ---------------------------------------------------------------------------
 // public API
 // ---------------------------------------------------------------------------
+// one guarded store for gbc_check_selftest
+namespace {
+__device__ int g_check_selftest_buf[64];
+__global__ void k_check_selftest(long long i) {
+  if (GBC_IN_RANGE(GBC_SITE_SELFTEST, i, 64)) g_check_selftest_buf[i] = 1;
+}
+}  // namespace
+
 extern "C" {
 
 const char* gbc_version(void) { return "gbchfsi 0.1 (sm_103a)"; }
@@ -459,10 +462,9 @@ void gbc_destroy(gbc_ctx* c) {
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
   void* ptrs[] = {c->d_md, c->d_invmd, c->d_invmd32, c->d_rawfields, c->d_fields64, c->d_fields32,
-                  c->work[0], c->work[1], c->work[2], c->work[3], c->work[4], c->work[5],
-                  c->work[6], c->work[7], c->work[8], c->work[9], c->d_small, c->d_flag,
-                  c->d_face_rows, c->d_cell_ctr};
+                  c->d_small, c->d_flag, c->d_face_rows, c->d_cell_ctr};
   for (void* p : ptrs) cudaFree(p);
+  for (void* p : c->work) cudaFree(p);
   delete c;
 }
 
@@ -601,6 +603,43 @@ gbc_status gbc_sync_status(gbc_ctx* c, void* stream) {
     GBC_CU(c, cudaStreamSynchronize(s));
     return gbc_fail(c, GBC_ETIMEOUT, "a tensor-core wait expired; results since the last check are invalid");
   }
+  // checked build: the first index out of range of every translation unit (all read,
+  // so all are cleared)
+  using Reader = cudaError_t (*)(unsigned long long*, cudaStream_t);
+  static const Reader readers[] = {gbc_check_word_cell0, gbc_check_word_cell1, gbc_check_word_cell2,
+                                   gbc_check_word_cell3, gbc_check_word_hx64,  gbc_check_word_blas,
+                                   gbc_check_word_nl,    gbc_check_word_nltc,  gbc_check_word_api};
+  unsigned long long first = 0;
+  for (Reader rd : readers) {
+    unsigned long long w = 0;
+    GBC_CU(c, rd(&w, s));
+    if (w && !first) first = w;
+  }
+  if (first) {
+    static const char* site[] = {"?", "FP32 cell apply (gather)", "FP32 cell apply (assembly)",
+                                 "face-row recurrence", "nonlocal support node", "nonlocal P table",
+                                 "FP64 cell apply", "self-test"};
+    const int st = (int)(first >> 48);
+    const long long idx = (long long)(first & 0xFFFFFFFFFFFFULL);
+    return gbc_fail(c, GBC_ECHECK, std::string("checked build: index ") + std::to_string(idx) +
+                                       " out of range at site " + std::to_string(st) + " (" +
+                                       site[(st >= 1 && st <= 7) ? st : 0] +
+                                       "); the access was skipped, results are invalid");
+  }
+  return GBC_OK;
+}
+
+gbc_status gbc_build_info(int* checked) {
+  if (!checked) return GBC_EINVAL;
+  *checked = GBC_CHECKED_BUILD;
+  return GBC_OK;
+}
+
+gbc_status gbc_check_selftest(long long index, void* stream) {
+  if (!GBC_CHECKED_BUILD && (index < 0 || index >= 64)) return GBC_EUNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_check_selftest<<<1, 1, 0, s>>>(index);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return GBC_ECUDA;
   return GBC_OK;
 }
 
@@ -793,3 +832,5 @@ gbc_status gbc_get_timing(gbc_ctx* c, int family, double* total_ms, long long* l
 }
 
 }  // extern "C"
+
+GBC_CHECK_WORD_ACCESSOR(gbc_check_word_api)

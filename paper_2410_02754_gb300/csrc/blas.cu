@@ -402,9 +402,10 @@ __global__ void k_convert(const A* __restrict__ X, int ldx, B* __restrict__ Out,
 }
 
 // ---- FP64 vector helpers (Lanczos) -------------------------------------------
-// out += sum_I md[I] sum_s conj(a[I][s]) b[I][s]   (n = M spinors)
+// out += sum_I md[I] sum_s conj(a[I][s]) b[I][s]   (n = M spinors); with part, each
+// block's sum goes to part[blockIdx.x] instead (k_sum_parts adds them in order)
 __global__ void k_mdot(const double2* __restrict__ a, const double2* __restrict__ b,
-                       const double* __restrict__ md, long long n, double2* out) {
+                       const double* __restrict__ md, long long n, double2* out, double2* part) {
   __shared__ double2 red[256];
   double2 acc = make_double2(0, 0);
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < n;
@@ -426,9 +427,23 @@ __global__ void k_mdot(const double2* __restrict__ a, const double2* __restrict_
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    atomicAdd(&out->x, red[0].x);
-    atomicAdd(&out->y, red[0].y);
+    if (part) {
+      part[blockIdx.x] = red[0];
+    } else {
+      atomicAdd(&out->x, red[0].x);
+      atomicAdd(&out->y, red[0].y);
+    }
   }
+}
+
+// out = sum_b part[b], b = 0 .. nb-1 in order (one thread)
+__global__ void k_sum_parts(const double2* __restrict__ part, int nb, double2* out) {
+  double2 acc = make_double2(0, 0);
+  for (int b = 0; b < nb; ++b) {
+    acc.x += part[b].x;
+    acc.y += part[b].y;
+  }
+  *out = acc;
 }
 
 // y -= (alpha_scale * alpha) x   (alpha read on the device)
@@ -474,14 +489,15 @@ inline unsigned grid_for(long long n, int threads = 256) {
 template <typename T>
 __global__ void k_cheb_rows(cplx<T>* __restrict__ Y, const cplx<T>* Xcur, const cplx<T>* Xprev,
                             cplx<T>* Xout, const T* __restrict__ invmd,
-                            const long long* __restrict__ rows, long long nrows, int nvec, int ldx,
-                            T a, T cshift, T b) {
+                            const long long* __restrict__ rows, long long nrows, long long M,
+                            int nvec, int ldx, T a, T cshift, T b) {
   const long long n = nrows * 2 * (long long)nvec;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const long long rs = i / nvec;
     const int v = (int)(i - rs * nvec);
     const long long node = rows[rs >> 1];
+    if (!GBC_IN_RANGE(GBC_SITE_FACE_ROW, node, M)) continue;
     const long long o = (node * 2 + (rs & 1)) * ldx + v;
     const T w = invmd[node];
     const cplx<T> y = Y[o];
@@ -501,20 +517,20 @@ __global__ void k_cheb_rows(cplx<T>* __restrict__ Y, const cplx<T>* Xcur, const 
 
 template <typename T>
 cudaError_t launch_cheb_rows(cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev, cplx<T>* Xout,
-                             const T* invmd, const long long* rows, long long nrows, int nvec,
-                             int ldx, double a, double cshift, double b, cudaStream_t s) {
+                             const T* invmd, const long long* rows, long long nrows, long long M,
+                             int nvec, int ldx, double a, double cshift, double b, cudaStream_t s) {
   if (nrows <= 0 || nvec <= 0) return cudaSuccess;
   k_cheb_rows<T><<<grid_for(nrows * 2 * nvec), 256, 0, s>>>(Y, Xcur, Xprev, Xout, invmd, rows,
-                                                            nrows, nvec, ldx, (T)a, (T)cshift,
+                                                            nrows, M, nvec, ldx, (T)a, (T)cshift,
                                                             (T)b);
   return cudaGetLastError();
 }
 template cudaError_t launch_cheb_rows<float>(float2*, const float2*, const float2*, float2*,
-                                             const float*, const long long*, long long, int, int,
-                                             double, double, double, cudaStream_t);
+                                             const float*, const long long*, long long, long long,
+                                             int, int, double, double, double, cudaStream_t);
 template cudaError_t launch_cheb_rows<double>(double2*, const double2*, const double2*, double2*,
-                                              const double*, const long long*, long long, int,
-                                              int, double, double, double, cudaStream_t);
+                                              const double*, const long long*, long long, long long,
+                                              int, int, double, double, double, cudaStream_t);
 
 // launch_cheb_rows over several systems in one launch (batched filter)
 template <typename T>
@@ -529,6 +545,7 @@ __global__ void k_cheb_rows_batch(const __grid_constant__ ChebRowsBatch b) {
     const long long rs = li / j.nvec;
     const int v = (int)(li - rs * j.nvec);
     const long long node = j.rows[rs >> 1];
+    if (!GBC_IN_RANGE(GBC_SITE_FACE_ROW, node, j.M)) continue;
     const long long o = (node * 2 + (rs & 1)) * j.ldx + v;
     cplx<T>* Y = (cplx<T>*)j.Y;
     const cplx<T> y = Y[o];
@@ -792,12 +809,19 @@ INST_SPLIT(float)
 INST_SPLIT(double)
 
 cudaError_t launch_mdot(const double2* a, const double2* b, const double* md, long long n,
-                        double2* out, cudaStream_t s) {
+                        double2* out, cudaStream_t s, double2* part) {
+  const unsigned nb = grid_for(n);
+  if (part) {
+    k_mdot<<<nb, 256, 0, s>>>(a, b, md, n, out, part);
+    k_sum_parts<<<1, 1, 0, s>>>(part, (int)nb, out);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double2), s);
   if (e != cudaSuccess) return e;
-  k_mdot<<<grid_for(n), 256, 0, s>>>(a, b, md, n, out);
+  k_mdot<<<nb, 256, 0, s>>>(a, b, md, n, out, nullptr);
   return cudaGetLastError();
 }
+size_t mdot_part_bytes(long long n) { return sizeof(double2) * grid_for(n); }
 cudaError_t launch_axpy_c(double2* y, const double2* x, const double2* alpha_dev,
                           double alpha_scale, long long n, cudaStream_t s) {
   k_axpy_c<<<grid_for(n), 256, 0, s>>>(y, x, alpha_dev, alpha_scale, n);
@@ -825,3 +849,5 @@ cudaError_t launch_divmass(double2* y, const double* invmd, long long M, cudaStr
                                             cudaStream_t);
 INST(float)
 INST(double)
+
+GBC_CHECK_WORD_ACCESSOR(gbc_check_word_blas)

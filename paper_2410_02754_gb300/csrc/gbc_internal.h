@@ -16,6 +16,61 @@
 #define GBC_TC_MAX_SLOTS 16 // atoms per tensor-core expansion chunk
 
 // ---------------------------------------------------------------------------
+// checked build (-DGBCHFSI_CHECKED): the hot kernels check each node / row index
+// before they use it; the first index out of range is recorded with its site in the
+// translation unit's check word and the access is skipped.  gbc_sync_status reads and
+// clears the words (GBC_ECHECK).  The default build compiles every check to `true`.
+// ---------------------------------------------------------------------------
+enum GbcCheckSite {
+  GBC_SITE_CELL_GATHER = 1,   // FP32 cell apply: node of the X gather
+  GBC_SITE_CELL_STORE = 2,    // FP32 cell apply: node of the epilogue / assembly
+  GBC_SITE_FACE_ROW = 3,      // face-row recurrence: listed row
+  GBC_SITE_NL_NODE = 4,       // nonlocal projection / expansion: support node
+  GBC_SITE_NL_PTAB = 5,       // nonlocal: row of an atom's P table
+  GBC_SITE_HX64 = 6,          // FP64 cell apply: node of the gather / assembly
+  GBC_SITE_SELFTEST = 7       // gbc_check_selftest
+};
+#if defined(GBCHFSI_CHECKED) && defined(__CUDACC__)
+static __device__ unsigned long long g_gbc_check;
+__device__ __forceinline__ bool gbc_in_range(int site, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_gbc_check, 0ULL,
+            ((unsigned long long)(site & 0xFFFF) << 48) | ((unsigned long long)i & 0xFFFFFFFFFFFFULL));
+  return false;
+}
+#define GBC_IN_RANGE(site, i, n) gbc_in_range((site), (long long)(i), (long long)(n))
+// host: read (and clear) this translation unit's check word
+#define GBC_CHECK_WORD_ACCESSOR(name)                                                        \
+  cudaError_t name(unsigned long long* w, cudaStream_t s) {                                  \
+    cudaError_t e = cudaMemcpyFromSymbolAsync(w, g_gbc_check, sizeof(*w), 0,                 \
+                                              cudaMemcpyDeviceToHost, s);                    \
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);                                      \
+    if (e != cudaSuccess || *w == 0) return e;                                               \
+    const unsigned long long zero = 0;                                                       \
+    return cudaMemcpyToSymbol(g_gbc_check, &zero, sizeof(zero));                            \
+  }
+#define GBC_CHECKED_BUILD 1
+#else
+#define GBC_IN_RANGE(site, i, n) true
+#define GBC_CHECK_WORD_ACCESSOR(name)                                                        \
+  cudaError_t name(unsigned long long* w, cudaStream_t) {                                    \
+    *w = 0;                                                                                  \
+    return cudaSuccess;                                                                      \
+  }
+#define GBC_CHECKED_BUILD 0
+#endif
+// the translation units with checked kernels
+cudaError_t gbc_check_word_cell0(unsigned long long* w, cudaStream_t s);
+cudaError_t gbc_check_word_cell1(unsigned long long* w, cudaStream_t s);
+cudaError_t gbc_check_word_cell2(unsigned long long* w, cudaStream_t s);
+cudaError_t gbc_check_word_cell3(unsigned long long* w, cudaStream_t s);
+cudaError_t gbc_check_word_hx64(unsigned long long* w, cudaStream_t s);
+cudaError_t gbc_check_word_blas(unsigned long long* w, cudaStream_t s);
+cudaError_t gbc_check_word_nl(unsigned long long* w, cudaStream_t s);
+cudaError_t gbc_check_word_nltc(unsigned long long* w, cudaStream_t s);
+cudaError_t gbc_check_word_api(unsigned long long* w, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // complex helpers (float2 / double2 carry (re, im))
 // ---------------------------------------------------------------------------
 template <typename T> struct cplx_t;
@@ -81,6 +136,7 @@ struct HostTables {
 struct ProjDev {
   int natoms = 0;
   int max_npj = 0;
+  long long M = 0;                   // free nodes of the mesh the tables index
   long long nnodes_total = 0;        // sum over atoms of support-node counts
   long long nentries = 0;
   // host copies of small per-atom metadata
@@ -150,10 +206,12 @@ struct gbc_ctx {
   // workspaces
   // 0 H.X accumulator, 1 second block, 2 nonlocal coefficients, 3 small dense,
   // 4-7 FP64 copies / residual-split blocks, 8 backward block pool, 9 backward
-  // accumulators
-  void* work[10] = {nullptr, nullptr, nullptr, nullptr, nullptr,
-                    nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t work_bytes[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // accumulators; deterministic mode: 10 per-cell results, 11 projection partials,
+  // 12 reduction partials
+  static constexpr int kWorkSlots = 13;
+  void* work[kWorkSlots] = {};
+  size_t work_bytes[kWorkSlots] = {};
+  bool deterministic = false;        // FP64 kernels: fixed-order sums instead of atomics
   void* d_small = nullptr;           // small dense scratch (Gram, eigensolver)
   size_t small_bytes = 0;
   int* d_flag = nullptr;
@@ -218,6 +276,7 @@ struct HxJob {
   const void* X;
   void* Y;
   int nvec, ldx;
+  void* Ycell = nullptr;   // non-null: per-cell results [E][n_p^3][2][nvec], no assembly
 };
 cudaError_t launch_hx_local_group_f64(const HxJob* jobs, int n, int vb, cudaStream_t s);
 // hx_cell_*.cu : FP32 cell apply (paired FP32 arithmetic).  Accumulate mode
@@ -293,8 +352,8 @@ cudaError_t launch_cheb_step(const cplx<T>* Y, const cplx<T>* Xcur, const cplx<T
 // the same update restricted to the listed rows (node indices), Y zeroed there
 template <typename T>
 cudaError_t launch_cheb_rows(cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev, cplx<T>* Xout,
-                             const T* invmd, const long long* rows, long long nrows, int nvec,
-                             int ldx, double a, double cshift, double b, cudaStream_t s);
+                             const T* invmd, const long long* rows, long long nrows, long long M,
+                             int nvec, int ldx, double a, double cshift, double b, cudaStream_t s);
 gbc_status setup_face_rows(gbc_ctx* c);
 #define GBC_MAX_CHEB_BATCH 32
 // the row update of several systems in one launch
@@ -306,6 +365,7 @@ struct ChebRowsJob {
   const void* invmd;
   const long long* rows;
   long long start;     // first flat element (listed row x spin x vector) of this job
+  long long M;         // nodes of the system (the rows' bound)
   int nvec, ldx;
   double a, c, b;
 };
@@ -384,8 +444,10 @@ cudaError_t launch_rotate_ff(const float2* X, const double2* Q, float2* Qsplit, 
 // Hermitian matrix from its upper triangle (the lower one mirrored, real diagonal)
 cudaError_t launch_hermitize(double2* A, int n, cudaStream_t s);
 // lanczos helpers
+// deterministic mode (part: scratch of mdot_part_bytes(n)): block sums added in order
 cudaError_t launch_mdot(const double2* a, const double2* b, const double* md, long long n,
-                        double2* out, cudaStream_t s);
+                        double2* out, cudaStream_t s, double2* part = nullptr);
+size_t mdot_part_bytes(long long n);
 cudaError_t launch_axpy_c(double2* y, const double2* x, const double2* alpha_dev, double alpha_scale,
                           long long n, cudaStream_t s);
 cudaError_t launch_scale_c(double2* y, const double2* x, double scale, long long n, cudaStream_t s);

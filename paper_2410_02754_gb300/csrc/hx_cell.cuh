@@ -272,7 +272,7 @@ __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int n
       const int v = i % VB, r = i / VB, s = r & 1, n = r >> 1;
       const int ix = n % NP, iy = (n / NP) % NP, iz = n / (NP * NP);
       const int I = no[ix] + no[NP + iy] + no[2 * NP + iz];
-      const bool ok = I >= 0 && vb0 + v < g.nvec;
+      const bool ok = I >= 0 && vb0 + v < g.nvec && GBC_IN_RANGE(GBC_SITE_CELL_GATHER, I, g.mesh.M);
       cp_async8(&Ab(v)[2 * pa(ix, iy, iz) + s],
                 ok ? &g.X[((long long)I * 2 + s) * g.ldx + vb0 + v] : g.X, ok ? 8 : 0);
     }
@@ -466,10 +466,15 @@ __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int n
         for (int j = 0; j < NIN; ++j) {
           const int I = Iyz + no[1 + j];
           const long long o = ((long long)I * 2 + s) * d.ldx + vec;
-          yv[j] = d.Y[o];
-          xv[j] = __ldg(&d.X[o]);
-          wv[j] = __ldg(d.invmd + I);
-          pv[j] = d.Xprev ? d.Xprev[o] : make_float2(0.f, 0.f);
+          if (GBC_IN_RANGE(GBC_SITE_CELL_STORE, I, d.mesh.M)) {
+            yv[j] = d.Y[o];
+            xv[j] = __ldg(&d.X[o]);
+            wv[j] = __ldg(d.invmd + I);
+            pv[j] = d.Xprev ? d.Xprev[o] : make_float2(0.f, 0.f);
+          } else {
+            yv[j] = xv[j] = pv[j] = make_float2(0.f, 0.f);
+            wv[j] = 0.f;
+          }
         }
 #pragma unroll
         for (int j = 0; j < NIN; ++j) {
@@ -478,18 +483,20 @@ __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int n
           const float2 yt = p_add(yv[j], out[1 + j]);
           const float2 xn = p_fma(dup(-d.cb), pv[j],
                                   p_mul(dup(d.ca), p_fma(dup(-d.cc), xv[j], p_mul(dup(wv[j]), yt))));
-          d.Xout[o] = xn;
+          if (GBC_IN_RANGE(GBC_SITE_CELL_STORE, I, d.mesh.M)) d.Xout[o] = xn;
         }
 #pragma unroll
         for (int i = 0; i < NP; i += NP - 1) {   // the pencil's two face nodes
           const int I = Iyz + no[i];
-          if (I >= 0) atomicAdd(&d.Y[((long long)I * 2 + s) * d.ldx + vec], out[i]);
+          if (I >= 0 && GBC_IN_RANGE(GBC_SITE_CELL_STORE, I, d.mesh.M))
+            atomicAdd(&d.Y[((long long)I * 2 + s) * d.ldx + vec], out[i]);
         }
       } else {
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
           const int I = Iyz + no[i];
-          if (I >= 0) atomicAdd(&d.Y[((long long)I * 2 + s) * d.ldx + vec], out[i]);
+          if (I >= 0 && GBC_IN_RANGE(GBC_SITE_CELL_STORE, I, d.mesh.M))
+            atomicAdd(&d.Y[((long long)I * 2 + s) * d.ldx + vec], out[i]);
         }
       }
     }

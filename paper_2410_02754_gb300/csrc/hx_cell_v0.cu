@@ -5,3 +5,5 @@
 cudaError_t launch_cell_f32_v0(const CellJob* jobs, int n, cudaStream_t s) {
   return gbc::launch_cell_group<2, 256, 4, true>(jobs, n, s);
 }
+
+GBC_CHECK_WORD_ACCESSOR(gbc_check_word_cell0)

@@ -5,3 +5,5 @@
 cudaError_t launch_cell_f32_v3(const CellJob* jobs, int n, cudaStream_t s) {
   return gbc::launch_cell_group<2, 256, 3, false>(jobs, n, s);
 }
+
+GBC_CHECK_WORD_ACCESSOR(gbc_check_word_cell3)

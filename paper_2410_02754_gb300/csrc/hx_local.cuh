@@ -241,7 +241,7 @@ hx_local_kernel(const __grid_constant__ LocalArgs<T> a, const TablesEO<T, NP, NQ
         const int ix = i % NP, iy = (i / NP) % NP, iz = i / (NP * NP);
         const long long I = gbc_node(d.mesh, cx, cy, cz, ix, iy, iz);
         C u = cmake<C>(0, 0), dn = cmake<C>(0, 0);
-        if (I >= 0 && vok) {
+        if (I >= 0 && vok && GBC_IN_RANGE(GBC_SITE_HX64, I, d.mesh.M)) {
           u = d.X[(I * 2 + 0) * d.ldx + vec];
           dn = d.X[(I * 2 + 1) * d.ldx + vec];
         }
@@ -402,7 +402,7 @@ hx_local_kernel(const __grid_constant__ LocalArgs<T> a, const TablesEO<T, NP, NQ
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
           const long long I = gbc_node(d.mesh, cx, cy, cz, i, y, z);
-          if (I < 0) continue;
+          if (I < 0 || !GBC_IN_RANGE(GBC_SITE_HX64, I, d.mesh.M)) continue;
           atomic_add_c<T>(&d.Y[(I * 2 + s) * d.ldx + vec], cadd(yacc[r][i], out[i]));
         }
       }

@@ -4,3 +4,5 @@
 cudaError_t launch_hx_local_group_f64(const HxJob* jobs, int n, int /*vb*/, cudaStream_t s) {
   return gbc::launch_hx_group<double, 1>(jobs, n, s);
 }
+
+GBC_CHECK_WORD_ACCESSOR(gbc_check_word_hx64)

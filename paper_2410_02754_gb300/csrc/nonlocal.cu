@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kCols)
 nl_project(const cplx<T>* __restrict__ X, int ldx, int nvec, const int4* __restrict__ chunks,
            const long long* __restrict__ nodes, const cplx<T>* __restrict__ P,
            const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off,
-           const int* __restrict__ atom_c_off, cplx<T>* __restrict__ Cbuf) {
+           const int* __restrict__ atom_c_off, cplx<T>* __restrict__ Cbuf, long long M) {
   using C = cplx<T>;
   __shared__ C Ps[kStage][MAXPJ];
   __shared__ long long Ns[kStage];
@@ -67,7 +67,8 @@ nl_project(const cplx<T>* __restrict__ X, int ldx, int nvec, const int4* __restr
         C x[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          x[u] = (t + u < nb) ? X[(Ns[t + u] * 2 + s) * ldx + v] : cmake<C>(0, 0);
+          x[u] = (t + u < nb && GBC_IN_RANGE(GBC_SITE_NL_NODE, Ns[t + u], M))
+                     ? X[(Ns[t + u] * 2 + s) * ldx + v] : cmake<C>(0, 0);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (t + u >= nb) break;
@@ -119,7 +120,7 @@ nl_expand(cplx<T>* __restrict__ Y, int ldx, int nvec, const int4* __restrict__ c
           const int* __restrict__ own_xptr, const int2* __restrict__ own_xinc,
           const cplx<T>* __restrict__ P, const int* __restrict__ atom_npj,
           const int* __restrict__ atom_pv_off, const int* __restrict__ atom_c_off,
-          const cplx<T>* __restrict__ Cp, int overwrite) {
+          const cplx<T>* __restrict__ Cp, int overwrite, long long M) {
   using C = cplx<T>;
   __shared__ C Ps[kExpStage][MAXPJ];
   const int4 ch = chunks[blockIdx.x];       // (atom, first owned index, count, -)
@@ -154,6 +155,7 @@ nl_expand(cplx<T>* __restrict__ Y, int ldx, int nvec, const int4* __restrict__ c
           const C* Cr = Cp + (size_t)(atom_c_off[inc.x] + s) * nvec + v;
           for (int c = 0; c < nb2; ++c) cmac(acc, Pr[c], Cr[(size_t)(2 * c) * nvec]);
         }
+        if (!GBC_IN_RANGE(GBC_SITE_NL_NODE, own_node[u], M)) continue;
         C* y = &Y[(own_node[u] * 2 + s) * ldx + v];
         if (overwrite) {
           *y = acc;
@@ -178,7 +180,7 @@ cudaError_t run_project(gbc_ctx* c, const cplx<T>* X, int nvec, int ldx, cplx<T>
   dim3 grid(pj.nchunks, (2 * nvec + kCols - 1) / kCols);
   nl_project<T, MAXPJ><<<grid, kCols, 0, s>>>(X, ldx, nvec, pj.d_chunks, pj.d_nodes, P,
                                               pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off,
-                                              Cbuf);
+                                              Cbuf, c->mesh.M);
   return cudaGetLastError();
 }
 
@@ -211,7 +213,7 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
   nl_expand<T, MP><<<g3, kCols, 0, s>>>(Y, ldx, nvec, pj.d_exp_chunks, pj.d_own_node,           \
                                         pj.d_own_pos, pj.d_own_xptr, pj.d_own_xinc, P,         \
                                         pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off, Cpbuf, \
-                                        overwrite ? 1 : 0)
+                                        overwrite ? 1 : 0, c->mesh.M)
   if (pj.max_npj <= 4) GBC_EXPAND(4);
   else if (pj.max_npj <= 8) GBC_EXPAND(8);
   else if (pj.max_npj <= 18) GBC_EXPAND(18);
@@ -253,3 +255,5 @@ size_t nl_work_bytes(const gbc_ctx* c, int nvec, int ldx, size_t el, size_t* bpr
   if (bpre_off) *bpre_off = xb ? off : 0;
   return std::max<size_t>(64, xb ? off + xb : 2 * cb);
 }
+
+GBC_CHECK_WORD_ACCESSOR(gbc_check_word_nl)

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(128, 4)
 k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __restrict__ chunks,
              const long long* __restrict__ nodes, const float2* __restrict__ P,
              const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off,
-             const int* __restrict__ atom_c_off, float2* __restrict__ Cbuf, int chunk0) {
+             const int* __restrict__ atom_c_off, float2* __restrict__ Cbuf, int chunk0, long long M) {
   static_assert(NB % 16 == 0 && NB >= 16 && NB <= 128, "NB");
   constexpr int NCOL = NB <= 32 ? 32 : NB <= 64 ? 64 : 128;   // per accumulator (D0, D1)
   constexpr int NBC = NB / 16;   // B float4 chunks per thread (NB rows x 8 chunks / 128)
@@ -171,7 +171,8 @@ k_tc_project(const float* __restrict__ Xr, int ldx, int nvec, const int4* __rest
   auto load = [&](float (&xa)[32], float (&xb)[NBC][4], int k0) {
 #pragma unroll
     for (int k = 0; k < 32; ++k)
-      xa[k] = (cok && k0 + k < cnt) ? __ldg(&Xr[Ns[k0 + k] * (long long)ncols + col]) : 0.f;
+      xa[k] = (cok && k0 + k < cnt && GBC_IN_RANGE(GBC_SITE_NL_NODE, Ns[k0 + k], M))
+                  ? __ldg(&Xr[Ns[k0 + k] * (long long)ncols + col]) : 0.f;
 #pragma unroll
     for (int i = 0; i < NBC; ++i) {
       const int q = tid + 128 * i, n = q >> 3, c = q & 7;
@@ -534,7 +535,7 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
             const int2* __restrict__ own_xinc, const float2* __restrict__ P,
             const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off,
             const int* __restrict__ atom_c_off, const float2* __restrict__ Cp, int chunk0,
-            int overwrite) {
+            int overwrite, long long M) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
   float4* Ahi = reinterpret_cast<float4*>(base);
@@ -572,6 +573,7 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
   if (tid < cnt) {   // slot 0 is the owner of every row of the chunk
     const int u = u0 + tid;
     s_node[tid] = own_node[u];
+    if (!GBC_IN_RANGE(GBC_SITE_NL_NODE, s_node[tid], M)) s_node[tid] = -1;   // checked build: skipped
     rowpos[tid] = own_pos[u];
     for (int k = own_xptr[u]; k < own_xptr[u + 1]; ++k) {
       const int2 inc = own_xinc[k];
@@ -647,13 +649,13 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
         for (int i = 0; i < 16; ++i) {
           const int r = rbase + 8 * i;
           yv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (r < cnt && !overwrite)
+          if (r < cnt && !overwrite && (!GBC_CHECKED_BUILD || s_node[r] >= 0))
             yv[i] = *reinterpret_cast<const float4*>(Yr + s_node[r] * (long long)ncols + gc);
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int r = rbase + 8 * i;
-          if (r < cnt) {
+          if (r < cnt && (!GBC_CHECKED_BUILD || s_node[r] >= 0)) {
             const float4 dv = *reinterpret_cast<const float4*>(Ds + r * kDsStride + 4 * (lane & 15));
             yv[i].x += dv.x;
             yv[i].y += dv.y;
@@ -665,6 +667,7 @@ k_tc_expand(float* __restrict__ Yr, int ldx, int nvec, int ks, const int4* __res
       } else {
 #pragma unroll 1
         for (int r = rbase; r < cnt; r += 8) {
+          if (GBC_CHECKED_BUILD && s_node[r] < 0) continue;
           const float* dv = Ds + r * kDsStride + 4 * (lane & 15);
           float* y = Yr + s_node[r] * (long long)ncols + gc;
 #pragma unroll
@@ -795,7 +798,7 @@ __device__ __forceinline__ bool wait_one(uint32_t mbar, uint32_t parity, volatil
 //   warps 2-5 epilogue: TMEM -> registers -> the thread's own staging row -> one bulk
 //             copy of the tile's 512 contiguous bytes of its node row; lane quadrant = warp % 4
 __global__ void __launch_bounds__(kXThreads, 1)
-k_tc_expand_ws(float* __restrict__ Yr, int ncols, int ntiles, int nchunks,
+k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int nchunks,
                const int4* __restrict__ chunks, const int* __restrict__ slots,
                const long long* __restrict__ own_node, const float* __restrict__ Apre,
                const float* __restrict__ Bpre) {
@@ -907,7 +910,8 @@ k_tc_expand_ws(float* __restrict__ Yr, int ncols, int ntiles, int nchunks,
     bool ok = true;
     for (int chn = blockIdx.x; chn < nchunks && ok; chn += gridDim.x) {
       const int4 ch = chunks[chn];
-      const long long node = r < ch.y ? own_node[ch.x + r] : -1;
+      long long node = r < ch.y ? own_node[ch.x + r] : -1;
+      if (node >= 0 && !GBC_IN_RANGE(GBC_SITE_NL_NODE, node, M)) node = -1;   // checked build
       for (int j = 0; j < ntiles; ++j, ++n) {
         const int acc = n & 1;
         if (!wait_uniform(tfull(acc), (n >> 1) & 1, abort_flag)) {
@@ -963,7 +967,7 @@ k_tc_expand_ws(float* __restrict__ Yr, int ncols, int ntiles, int nchunks,
 
 template <int NB>
 cudaError_t run_tc_project(const ProjDev& pj, const float2* X, int nvec, int ldx, float2* Cbuf,
-                           cudaStream_t s) {
+                           cudaStream_t s, long long M) {
   auto k = k_tc_project<NB>;
   constexpr size_t smem = project_smem<NB>();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -973,7 +977,7 @@ cudaError_t run_tc_project(const ProjDev& pj, const float2* X, int nvec, int ldx
     dim3 grid(ntile, (unsigned)std::min(kMaxGridY, pj.nchunks - c0));
     k<<<grid, 128, smem, s>>>(reinterpret_cast<const float*>(X), ldx, nvec, pj.d_chunks,
                               pj.d_nodes, pj.d_P32, pj.d_atom_npj, pj.d_atom_pv_off,
-                              pj.d_atom_c_off, Cbuf, c0);
+                              pj.d_atom_c_off, Cbuf, c0, M);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1051,14 +1055,14 @@ cudaError_t launch_tc_project(const ProjDev& pj, long long M, const float2* X, i
     }
   }
   switch (nb) {
-    case 16: return run_tc_project<16>(pj, X, nvec, ldx, Cbuf, s);
-    case 32: return run_tc_project<32>(pj, X, nvec, ldx, Cbuf, s);
-    case 48: return run_tc_project<48>(pj, X, nvec, ldx, Cbuf, s);
-    case 64: return run_tc_project<64>(pj, X, nvec, ldx, Cbuf, s);
-    case 80: return run_tc_project<80>(pj, X, nvec, ldx, Cbuf, s);
-    case 96: return run_tc_project<96>(pj, X, nvec, ldx, Cbuf, s);
-    case 112: return run_tc_project<112>(pj, X, nvec, ldx, Cbuf, s);
-    case 128: return run_tc_project<128>(pj, X, nvec, ldx, Cbuf, s);
+    case 16: return run_tc_project<16>(pj, X, nvec, ldx, Cbuf, s, M);
+    case 32: return run_tc_project<32>(pj, X, nvec, ldx, Cbuf, s, M);
+    case 48: return run_tc_project<48>(pj, X, nvec, ldx, Cbuf, s, M);
+    case 64: return run_tc_project<64>(pj, X, nvec, ldx, Cbuf, s, M);
+    case 80: return run_tc_project<80>(pj, X, nvec, ldx, Cbuf, s, M);
+    case 96: return run_tc_project<96>(pj, X, nvec, ldx, Cbuf, s, M);
+    case 112: return run_tc_project<112>(pj, X, nvec, ldx, Cbuf, s, M);
+    case 128: return run_tc_project<128>(pj, X, nvec, ldx, Cbuf, s, M);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1094,7 +1098,7 @@ cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, co
     e = cudaFuncSetAttribute(k_tc_expand_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min(pj.ntc_exp, gbc_sm_count());
-    k_tc_expand_ws<<<grid, kXThreads, smem, s>>>(reinterpret_cast<float*>(Y), 4 * ldx, ntiles, pj.ntc_exp,
+    k_tc_expand_ws<<<grid, kXThreads, smem, s>>>(reinterpret_cast<float*>(Y), pj.M, 4 * ldx, ntiles, pj.ntc_exp,
                                                  pj.d_tcexp_chunks, pj.d_tcexp_slots, pj.d_own_node,
                                                  pj.d_xA, reinterpret_cast<const float*>(bpre));
     return cudaGetLastError();
@@ -1110,7 +1114,7 @@ cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, co
                                         pj.d_tcexp_chunks, pj.d_tcexp_slots, pj.d_own_node,
                                         pj.d_own_pos, pj.d_own_xptr, pj.d_own_xinc, pj.d_P32,
                                         pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off, Cp, c0,
-                                        overwrite ? 1 : 0);
+                                        overwrite ? 1 : 0, pj.M);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1151,3 +1155,5 @@ cudaError_t tc_nonlocal_error(int* err, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(s);
 }
+
+GBC_CHECK_WORD_ACCESSOR(gbc_check_word_nltc)

@@ -606,6 +606,7 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
   GBC_TRY(upload(c, (void**)&pj.d_exp_chunks, echunks.data(), sizeof(int4) * echunks.size()));
   pj.ntc_exp = (int)tcchunks.size();
   pj.ntc_slots = (long long)tcslots.size();
+  pj.M = c->mesh.M;
   pj.tc_max_slots = 0;
   for (const int4& q : tcchunks) pj.tc_max_slots = std::max(pj.tc_max_slots, q.w);
   GBC_TRY(upload(c, (void**)&pj.d_tcexp_chunks, tcchunks.data(), sizeof(int4) * tcchunks.size()));

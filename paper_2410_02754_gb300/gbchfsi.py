@@ -5,7 +5,9 @@ kernels.  Device blocks are torch CUDA tensors used as plain memory:
 complex128 for ``FP64``, complex64 for ``FP32``, shape [M, 2, ldx] (or a
 contiguous view with that layout).  The library is loaded from this package
 directory; importing this module on a machine without the built library or
-without a CUDA device raises, there is no fallback.
+without a CUDA device raises, there is no fallback.  With GBCHFSI_CHECKED=1 in
+the environment the checked build (libgbchfsi_checked.so, device index checks)
+is loaded instead.
 """
 from __future__ import annotations
 
@@ -15,12 +17,13 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgbchfsi.so")
+LIB_PATH = os.path.join(_HERE, "libgbchfsi_checked.so" if os.environ.get("GBCHFSI_CHECKED") == "1"
+                        else "libgbchfsi.so")
 
 FP64, FP32 = 0, 1
 TF32, BF16X3 = 2, 3          # FP32 blocks, cell products as tcgen05 GEMMs (single TF32 / BF16 x3)
 STATUS = {0: "GBC_OK", 1: "GBC_EINVAL", 2: "GBC_ENOMEM", 3: "GBC_ECUDA", 4: "GBC_ESTATE",
-          5: "GBC_ENOTPD", 6: "GBC_ETIMEOUT", 7: "GBC_EUNSUPPORTED"}
+          5: "GBC_ENOTPD", 6: "GBC_ETIMEOUT", 7: "GBC_EUNSUPPORTED", 8: "GBC_ECHECK"}
 
 # every entry point declared in include/gbchfsi.h
 EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_set_mesh",
@@ -35,7 +38,7 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_sync_status", "gbc_density", "gbc_density_dev", "gbc_fermi_occupations",
            "gbc_prolongate", "gbc_scf_fields", "gbc_anderson_mix", "gbc_get_ndof",
            "gbc_filter_backward", "gbc_alu_peak", "gbc_set_cell_variant",
-           "gbc_get_cell_variant"]
+           "gbc_get_cell_variant", "gbc_build_info", "gbc_check_selftest"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -54,7 +57,8 @@ def load_library(path: str = LIB_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"libgbchfsi.so not built at {path}; run __graft_entry__.build()")
+        raise ImportError(f"{os.path.basename(path)} not built at {path}; run __graft_entry__.build()"
+                          " (the checked build: paper_2410_02754_gb300._build.build(checked=True))")
     lib = ct.CDLL(path)
     P, I, D, V = ct.c_void_p, ct.c_int, ct.c_double, ct.c_void_p
     IP, DP = ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)
@@ -98,6 +102,8 @@ def load_library(path: str = LIB_PATH):
         "gbc_anderson_mix": ([P, ct.POINTER(V), ct.POINTER(V), I, D, V, DP, DP, V], I),
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
         "gbc_tc_wait_selftest": ([I, V], I),
+        "gbc_build_info": ([IP], I),
+        "gbc_check_selftest": ([ct.c_longlong, V], I),
         "gbc_set_nonlocal_engine": ([P, I], I),
         "gbc_get_nonlocal_engine": ([P, IP], I),
         "gbc_sync_status": ([P, V], I),
@@ -547,6 +553,22 @@ def alu_peak(which, stream=None):
     if st != 0:
         raise GbcError(st, f"gbc_alu_peak({which}) failed")
     return rate.value, sec.value
+
+
+def build_info():
+    """{'checked': True} for the checked build (device index checks), else False."""
+    v = ct.c_int()
+    st = load_library().gbc_build_info(ct.byref(v))
+    if st != 0:
+        raise GbcError(st, "gbc_build_info failed")
+    return {"checked": bool(v.value)}
+
+
+def check_selftest(index, stream=None):
+    """One guarded store at ``index`` into a 64-entry device array (gbc_check_selftest);
+    returns the status code (0, or 7 = GBC_EUNSUPPORTED outside [0, 64) in the default
+    build)."""
+    return load_library().gbc_check_selftest(int(index), _stream_ptr(stream))
 
 
 def tc_wait_selftest(max_iter=1000, stream=None):
