@@ -342,7 +342,11 @@ def run_gpu(args):
             a[1] += n
         c.set_timing(False)
     # kernels per family launch: local 1, nonlocal 3 (project, couple, expand), epilogue 1
-    launches = fams["hx_local"][1] + 3 * fams["nonlocal"][1] + fams["cheb"][1]
+    # nonlocal family: projection, coupling and expansion, plus the packing of C' when the
+    # tensor engine expands from packed operands (2 n_pj <= 40, ldx = nvec)
+    packed = (ctx32[0].nonlocal_engine() == 1 and prob.atoms
+              and 2 * max(a.npj for a in prob.atoms) <= 40)
+    launches = fams["hx_local"][1] + (4 if packed else 3) * fams["nonlocal"][1] + fams["cheb"][1]
     launches += (degree % 2) * len(ks) * args.steps      # final block copy for odd degree
     tot = sum(v[0] for v in fams.values()) or 1.0
     kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1],

@@ -412,6 +412,27 @@ gbc_status gbc_tc_gemm_nt(const float* A, const float* B, float* D, int M, int N
  * stays usable.  Synchronous; GBC_EINVAL for a cap out of range. */
 gbc_status gbc_tc_wait_selftest(int max_iter, void* stream);
 
+/* ---- deterministic mode ------------------------------------------------------------
+ * With ``on`` != 0 the context's FP64 kernels add in a fixed order instead of with
+ * atomics, so FP64 H.X, the FP64 filter, the Lanczos bounds, the energy gradient and
+ * the filter's vector-Jacobian product give the same bits on every run (for comparing
+ * against the default atomic mode, which differs from it by rounding only):
+ *   - cell apply: each cell's result goes to a per-cell buffer ([E][n_p^3][2][nvec],
+ *     FP64), then each node adds the results of the cells holding it in a fixed order
+ *     (instead of FP64 atomics into Y);
+ *   - nonlocal projection C = P^H X (FP64 and the FP32 SIMT engine): per support chunk,
+ *     then each atom's chunks added in order;
+ *   - the column dots of the energy and the M_D inner products of the Lanczos process:
+ *     block sums added in order;
+ *   - the projector tables P (set-up): the support cells of each atom added in order
+ *     (switching the mode rebuilds them on the next call).
+ * Not covered: the FP32 cell apply (atomics on cell-face nodes), the tensor-core
+ * projection, the Gram matrices of CholGS / Rayleigh-Ritz, the batched and the
+ * allocation-free entry points.  Allocates the per-cell buffer on first use (16 E n_p^3
+ * 2 nvec bytes).  A debugging and reproducibility aid; no counterpart in the paper. */
+gbc_status gbc_set_deterministic(gbc_ctx* ctx, int on);
+gbc_status gbc_get_deterministic(const gbc_ctx* ctx, int* on);
+
 /* ---- checked build ---------------------------------------------------------------
  * The same sources compiled with -DGBCHFSI_CHECKED give libgbchfsi_checked.so (the
  * Python binding loads it when GBCHFSI_CHECKED=1): before each node or row index is used,

@@ -122,7 +122,14 @@ gbc_status apply_h_t(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, int ldx
   cudaError_t e;
   {
     TimerScope ts(c, FAM_HX_LOCAL, s);
-    if (std::is_same<T, double>::value) {
+    if (std::is_same<T, double>::value && c->deterministic) {
+      // per-cell results, then every node's cell contributions added in a fixed order
+      const long long np = c->mesh.p + 1;
+      GBC_TRY(gbc_ensure_work(c, 10, sizeof(double2) * (size_t)c->mesh.E * np * np * np * 2 * nvec));
+      e = launch_hx_local_f64(c, (const double2*)X, (double2*)Y, nvec, ldx, s, c->work[10]);
+      if (e == cudaSuccess)
+        e = launch_cell_gather_f64(c, (const double2*)c->work[10], (double2*)Y, nvec, ldx, s);
+    } else if (std::is_same<T, double>::value) {
       e = launch_hx_local_f64(c, (const double2*)X, (double2*)Y, nvec, ldx, s);
     } else if (c->prec == GBC_TF32 || c->prec == GBC_BF16X3) {
       GBC_TRY(tcl_apply(c, (const float2*)X, (float2*)Y, nvec, ldx, c->prec == GBC_BF16X3 ? 1 : 0, s));
@@ -575,6 +582,19 @@ gbc_status gbc_set_precision(gbc_ctx* c, gbc_precision prec) {
   return GBC_OK;
 }
 
+gbc_status gbc_set_deterministic(gbc_ctx* c, int on) {
+  if (!c) return GBC_EINVAL;
+  if (c->deterministic != (on != 0) && c->proj.natoms > 0) c->proj_dirty = true;   // P rebuilt
+  c->deterministic = on != 0;
+  return GBC_OK;
+}
+
+gbc_status gbc_get_deterministic(const gbc_ctx* c, int* on) {
+  if (!c || !on) return GBC_EINVAL;
+  *on = c->deterministic ? 1 : 0;
+  return GBC_OK;
+}
+
 gbc_status gbc_set_nonlocal_engine(gbc_ctx* c, int engine) {
   if (!c) return GBC_EINVAL;
   if (engine != GBC_NL_SIMT && engine != GBC_NL_TENSOR)
@@ -745,7 +765,12 @@ gbc_status gbc_lanczos_bounds(gbc_ctx* c, const void* v0, int steps, double* lmi
   const long long n2 = 2 * M;
   // v_1 = v0 / ||v0||_M
   double2 h;
-  GBC_CU(c, launch_mdot((const double2*)v0, (const double2*)v0, c->d_md, M, coef, s));
+  double2* part = nullptr;   // deterministic mode: block sums added in order
+  if (c->deterministic) {
+    GBC_TRY(gbc_ensure_work(c, 12, mdot_part_bytes(M)));
+    part = (double2*)c->work[12];
+  }
+  GBC_CU(c, launch_mdot((const double2*)v0, (const double2*)v0, c->d_md, M, coef, s, part));
   GBC_CU(c, cudaMemcpyAsync(&h, coef, sizeof(double2), cudaMemcpyDeviceToHost, s));
   GBC_CU(c, cudaStreamSynchronize(s));
   if (!(h.x > 0)) return gbc_fail(c, GBC_EINVAL, "zero start vector");
@@ -758,7 +783,7 @@ gbc_status gbc_lanczos_bounds(gbc_ctx* c, const void* v0, int steps, double* lmi
     GBC_CU(c, launch_divmass(w, c->d_invmd, M, s));
     // alpha_j = <v_j, w>_M ; w -= alpha v_j + beta_{j-1} v_{j-1}; two passes of full
     // reorthogonalisation against v_0..v_j
-    GBC_CU(c, launch_mdot(vj, w, c->d_md, M, coef, s));
+    GBC_CU(c, launch_mdot(vj, w, c->d_md, M, coef, s, part));
     GBC_CU(c, cudaMemcpyAsync(&h, coef, sizeof(double2), cudaMemcpyDeviceToHost, s));
     GBC_CU(c, cudaStreamSynchronize(s));
     alpha[j] = h.x;
@@ -766,11 +791,11 @@ gbc_status gbc_lanczos_bounds(gbc_ctx* c, const void* v0, int steps, double* lmi
     for (int pass = 0; pass < 2; ++pass) {
       for (int i = 0; i <= j; ++i) {
         double2* vi = V + (size_t)i * n2;
-        GBC_CU(c, launch_mdot(vi, w, c->d_md, M, coef + 1 + i, s));
+        GBC_CU(c, launch_mdot(vi, w, c->d_md, M, coef + 1 + i, s, part));
         GBC_CU(c, launch_axpy_c(w, vi, coef + 1 + i, 1.0, n2, s));
       }
     }
-    GBC_CU(c, launch_mdot(w, w, c->d_md, M, coef, s));
+    GBC_CU(c, launch_mdot(w, w, c->d_md, M, coef, s, part));
     GBC_CU(c, cudaMemcpyAsync(&h, coef, sizeof(double2), cudaMemcpyDeviceToHost, s));
     GBC_CU(c, cudaStreamSynchronize(s));
     beta[j] = std::sqrt(std::max(h.x, 0.0));

@@ -25,8 +25,8 @@
 // single-system cell apply with the context's tile
 // ---------------------------------------------------------------------------
 cudaError_t launch_hx_local_f64(const gbc_ctx* c, const double2* X, double2* Y, int nvec, int ldx,
-                                cudaStream_t s) {
-  HxJob j{c, X, Y, nvec, ldx};
+                                cudaStream_t s, void* Ycell) {
+  HxJob j{c, X, Y, nvec, ldx, Ycell};
   return launch_hx_local_group_f64(&j, 1, 1, s);
 }
 

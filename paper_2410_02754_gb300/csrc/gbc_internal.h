@@ -155,6 +155,7 @@ struct ProjDev {
   // chunk table for the projection kernel: (atom, first node, count)
   int nchunks = 0;
   int4* d_chunks = nullptr;
+  int* d_chunk_off = nullptr;        // [natoms+1] each atom's chunks (consecutive)
   // expansion: every distinct support node is owned by the lowest-index atom
   // holding it; owned nodes grouped by owner, with the other atoms' incidences
   long long nuniq = 0;
@@ -279,6 +280,9 @@ struct HxJob {
   void* Ycell = nullptr;   // non-null: per-cell results [E][n_p^3][2][nvec], no assembly
 };
 cudaError_t launch_hx_local_group_f64(const HxJob* jobs, int n, int vb, cudaStream_t s);
+// Y += the per-cell results Ycell of launch_hx_local_group_f64, in a fixed order per node
+cudaError_t launch_cell_gather_f64(const gbc_ctx* c, const double2* Ycell, double2* Y, int nvec,
+                                   int ldx, cudaStream_t s);
 // hx_cell_*.cu : FP32 cell apply (paired FP32 arithmetic).  Accumulate mode
 // (Xout == null): Y += H^loc X.  Recurrence mode: nodes interior to a cell get
 // X_out = a (M_D^-1 (Y + (H^loc X)_row) - cshift X) - b X_prev directly, face
@@ -298,8 +302,9 @@ struct CellVariant { int vb, nt, minb, packed; };
 CellVariant cell_variant(int v);
 cudaError_t launch_cell_f32(const CellJob* jobs, int n, int variant, cudaStream_t s);
 // single system, tile chosen by the context's tuned setting
+// (Ycell non-null: per-cell results, no assembly; see launch_cell_gather_f64)
 cudaError_t launch_hx_local_f64(const gbc_ctx* c, const double2* X, double2* Y, int nvec, int ldx,
-                                cudaStream_t s);
+                                cudaStream_t s, void* Ycell = nullptr);
 cudaError_t launch_hx_local_f32(const gbc_ctx* c, const float2* X, float2* Y, int nvec, int ldx,
                                 cudaStream_t s);
 // tc_cell.cu : Y += H^loc X for an FP32 block with the cell products as tcgen05

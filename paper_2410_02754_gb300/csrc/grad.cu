@@ -58,10 +58,11 @@ __global__ void k_colscale(cplx<T>* G, const double* __restrict__ w, double f, l
   }
 }
 
-// dots[v] += sum_rows Re(conj(A[row][v]) B[row][v])  (FP64 accumulation)
+// dots[v] += sum_rows Re(conj(A[row][v]) B[row][v])  (FP64 accumulation); with part,
+// block x's sum goes to part[x][v] instead (k_coldot_parts adds them in order)
 template <typename T>
 __global__ void k_coldot(const cplx<T>* __restrict__ A, const cplx<T>* __restrict__ B,
-                         long long rows, int nvec, int ldx, double* dots) {
+                         long long rows, int nvec, int ldx, double* dots, double* part) {
   const int v = blockIdx.y * blockDim.x + threadIdx.x;
   if (v >= nvec) return;
   double acc = 0.0;
@@ -69,7 +70,17 @@ __global__ void k_coldot(const cplx<T>* __restrict__ A, const cplx<T>* __restric
     const cplx<T> a = A[r * ldx + v], b = B[r * ldx + v];
     acc += (double)a.x * (double)b.x + (double)a.y * (double)b.y;
   }
-  atomicAdd(&dots[v], acc);
+  if (part) part[(size_t)blockIdx.x * nvec + v] = acc;
+  else atomicAdd(&dots[v], acc);
+}
+
+// dots[v] += sum_b part[b][v], b = 0 .. nb-1 in order
+__global__ void k_coldot_parts(const double* __restrict__ part, int nb, int nvec, double* dots) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvec) return;
+  double acc = 0.0;
+  for (int b = 0; b < nb; ++b) acc += part[(size_t)b * nvec + v];
+  dots[v] += acc;
 }
 
 // gD[atom][r][s] += f * sum_v wv[v] Ca[r][v] conj(Cb[s][v])   (rows c_off + r)
@@ -308,8 +319,17 @@ gbc_status energy_grad_t(gbc_ctx* c, const cplx<T>* Y, const double* w, cplx<T>*
   // H Y -> GY, the loss from the column dots, then G_Y = 2 H Y diag(w)
   GBC_TRY(gbc_apply_h_dev(c, Y, GY, nvec, ldx, true, s));
   dim3 gd((unsigned)std::min<long long>(rows, 4096), (nvec + 127) / 128);
-  k_coldot<T><<<gd, 128, 0, s>>>(Y, GY, rows, nvec, ldx, gs.dots);
+  double* part = nullptr;
+  if (c->deterministic) {
+    GBC_TRY(gbc_ensure_work(c, 12, sizeof(double) * gd.x * (size_t)nvec));
+    part = (double*)c->work[12];
+  }
+  k_coldot<T><<<gd, 128, 0, s>>>(Y, GY, rows, nvec, ldx, gs.dots, part);
   GBC_CU(c, cudaGetLastError());
+  if (part) {
+    k_coldot_parts<<<(nvec + 127) / 128, 128, 0, s>>>(part, (int)gd.x, nvec, gs.dots);
+    GBC_CU(c, cudaGetLastError());
+  }
   k_colscale<T><<<gfor(rows * nvec), 256, 0, s>>>(GY, gs.wv, 2.0, rows, nvec, ldx);
   GBC_CU(c, cudaGetLastError());
   GBC_CU(c, quad_grad<T>(c, Y, Y, gs.wv, 1.0, nvec, ldx, gs.g, s));

@@ -69,7 +69,7 @@ template <int NP, int NQ, bool PACKED> struct CellTables {
 struct CellSys {
   const float2* X;      // block applied to
   float2* Y;            // accumulator
-  const float* fields;  // [E][4][NQ^3] w_q J (V + |k|^2/2), w_q J B_x, B_y, B_z
+  const float* fields;  // [E][NQ^3][4] w_q J (V + |k|^2/2), w_q J B_x, B_y, B_z
   float2* Xout;         // recurrence mode: X_{k+1} (may alias Xprev)
   const float2* Xprev;  // recurrence mode: X_{k-1}, or null on the first step
   const float* invmd;   // recurrence mode: 1 / M_D per node
@@ -410,8 +410,8 @@ __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int n
           oth.x = __shfl_xor_sync(0xffffffffu, own[q].x, 1);
           oth.y = __shfl_xor_sync(0xffffffffu, own[q].y, 1);
           const int qq = (q * NQ + y) * NQ + x;
-          const float V = __ldg(fld + qq), bx = __ldg(fld + NQ3 + qq),
-                      by = __ldg(fld + 2 * NQ3 + qq), bz = __ldg(fld + 3 * NQ3 + qq);
+          const float4 F = __ldg(reinterpret_cast<const float4*>(fld) + qq);
+          const float V = F.x, bx = F.y, by = F.z, bz = F.w;
           // up:   (V + bz) u + bx d + by (d.y, -d.x)
           // down: (V - bz) d + bx u - by (u.y, -u.x)
           float2 o = p_mul(dup(V + sg * bz), own[q]);

@@ -30,6 +30,7 @@ namespace gbc {
 template <typename T> struct SysDesc {
   const cplx<T>* X;
   cplx<T>* Y;
+  cplx<T>* Ycell;    // non-null: per-cell results [E][n_p^3][2][nvec] instead of assembly
   const T* fields;   // [E][4][NQ^3]
   int ldx, nvec, vchunks, pad;
   long long item0;   // work items of this system: [item0, item0 + E * vchunks)
@@ -403,7 +404,11 @@ hx_local_kernel(const __grid_constant__ LocalArgs<T> a, const TablesEO<T, NP, NQ
         for (int i = 0; i < NP; ++i) {
           const long long I = gbc_node(d.mesh, cx, cy, cz, i, y, z);
           if (I < 0 || !GBC_IN_RANGE(GBC_SITE_HX64, I, d.mesh.M)) continue;
-          atomic_add_c<T>(&d.Y[(I * 2 + s) * d.ldx + vec], cadd(yacc[r][i], out[i]));
+          if (d.Ycell)
+            d.Ycell[(((long long)e * (NP * NP * NP) + i + NP * (y + NP * z)) * 2 + s) * d.nvec + vec] =
+                cadd(yacc[r][i], out[i]);
+          else
+            atomic_add_c<T>(&d.Y[(I * 2 + s) * d.ldx + vec], cadd(yacc[r][i], out[i]));
         }
       }
     }
@@ -419,6 +424,7 @@ template <typename T, int NP, int NQ, int VB> constexpr size_t hx_local_smem() {
 
 template <typename T, int NP, int VB>
 cudaError_t launch_hx_group_p(const HxJob* jobs, int n, cudaStream_t s) {
+  static_assert(std::is_same<T, double>::value, "FP64 only (the FP32 cell apply is hx_cell.cuh)");
   constexpr int NQ = NP + 1;   // nq = p + 2
   if (n < 1 || n > GBC_MAX_BATCH) return cudaErrorInvalidValue;
   LocalArgs<T> a;
@@ -433,7 +439,8 @@ cudaError_t launch_hx_group_p(const HxJob* jobs, int n, cudaStream_t s) {
     const gbc_ctx* c = jobs[i].c;
     d.X = (const cplx<T>*)jobs[i].X;
     d.Y = (cplx<T>*)jobs[i].Y;
-    d.fields = std::is_same<T, double>::value ? (const T*)c->d_fields64 : (const T*)c->d_fields32;
+    d.Ycell = (cplx<T>*)jobs[i].Ycell;
+    d.fields = (const T*)c->d_fields64;
     d.ldx = jobs[i].ldx;
     d.nvec = jobs[i].nvec;
     d.vchunks = (jobs[i].nvec + VB - 1) / VB;
@@ -466,6 +473,62 @@ cudaError_t launch_hx_group_p(const HxJob* jobs, int n, cudaStream_t s) {
   };
   if (kpt) return run(hx_local_kernel<T, NP, NQ, true, VB>);
   return run(hx_local_kernel<T, NP, NQ, false, VB>);
+}
+
+// Deterministic assembly: Y[I][s][v] += the results of every cell holding node I, added
+// in a fixed order (cells by direction z, y, x, lower neighbour first).  Along each
+// direction a node at grid index g is interior to cell g / p (local g % p), or, when
+// g % p == 0, shared by cell g / p - 1 (local p; periodic wrap at 0) and cell g / p
+// (local 0).
+template <typename T>
+__global__ void k_cell_gather(cplx<T>* __restrict__ Y, const cplx<T>* __restrict__ Ycell,
+                              const MeshDev m, int nvec, int ldx) {
+  const int np = m.p + 1;
+  const long long np3 = (long long)np * np * np;
+  const long long n = m.M * 2 * (long long)nvec;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(t % nvec);
+    const long long rs = t / nvec;
+    const int s = (int)(rs & 1);
+    const long long I = rs >> 1;
+    const long long f[3] = {I % m.nfree[0], (I / m.nfree[0]) % m.nfree[1],
+                            I / ((long long)m.nfree[0] * m.nfree[1])};
+    int cell[3][2], loc[3][2], cnt[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int g = (int)f[d] + (m.periodic[d] ? 0 : 1);
+      const int q = g / m.p, r = g % m.p;
+      if (r != 0) {
+        cell[d][0] = q;
+        loc[d][0] = r;
+        cnt[d] = 1;
+      } else {
+        cnt[d] = 0;
+        if (q > 0 || m.periodic[d]) {
+          cell[d][cnt[d]] = q > 0 ? q - 1 : m.ncell[d] - 1;
+          loc[d][cnt[d]++] = m.p;
+        }
+        if (q < m.ncell[d]) {
+          cell[d][cnt[d]] = q;
+          loc[d][cnt[d]++] = 0;
+        }
+      }
+    }
+    cplx<T> acc = cmake<cplx<T>>(0, 0);
+    for (int a = 0; a < cnt[2]; ++a)
+      for (int b = 0; b < cnt[1]; ++b)
+        for (int c = 0; c < cnt[0]; ++c) {
+          const long long e = cell[0][c] + (long long)m.ncell[0] * (cell[1][b] + (long long)m.ncell[1] * cell[2][a]);
+          const long long l = loc[0][c] + np * (loc[1][b] + np * loc[2][a]);
+          const cplx<T> y = Ycell[((e * np3 + l) * 2 + s) * nvec + v];
+          acc.x += y.x;
+          acc.y += y.y;
+        }
+    cplx<T>& o = Y[(I * 2 + s) * ldx + v];
+    o.x += acc.x;
+    o.y += acc.y;
+  }
 }
 
 // dispatch on p (nq = p + 2) for a fixed VB

@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(kCols)
 nl_project(const cplx<T>* __restrict__ X, int ldx, int nvec, const int4* __restrict__ chunks,
            const long long* __restrict__ nodes, const cplx<T>* __restrict__ P,
            const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off,
-           const int* __restrict__ atom_c_off, cplx<T>* __restrict__ Cbuf, long long M) {
+           const int* __restrict__ atom_c_off, cplx<T>* __restrict__ Cbuf, long long M,
+           cplx<T>* __restrict__ Cpart) {
   using C = cplx<T>;
   __shared__ C Ps[kStage][MAXPJ];
   __shared__ long long Ns[kStage];
@@ -80,12 +81,33 @@ nl_project(const cplx<T>* __restrict__ X, int ldx, int nvec, const int4* __restr
     }
     __syncthreads();
   }
-  if (ok) {
+  if (ok && Cpart) {   // this chunk's sums, rows 2chi + s (k_nl_chunk_sum adds them in order)
+#pragma unroll
+    for (int c = 0; c < MAXPJ; ++c)
+      if (c < npj) Cpart[((size_t)blockIdx.x * 2 * MAXPJ + 2 * c + s) * nvec + v] = acc[c];
+  } else if (ok) {
     const int r0 = atom_c_off[atom];
 #pragma unroll
     for (int c = 0; c < MAXPJ; ++c)
       if (c < npj) catomic(&Cbuf[(size_t)(r0 + 2 * c + s) * nvec + v], acc[c]);
   }
+}
+
+// C[(c_off + r) * nvec + v] = sum over the atom's chunks k, in order, of Cpart[k][r][v]
+template <typename T, int MAXPJ>
+__global__ void k_nl_chunk_sum(const cplx<T>* __restrict__ Cpart, cplx<T>* __restrict__ Cbuf,
+                               const int* __restrict__ chunk_off, const int* __restrict__ atom_npj,
+                               const int* __restrict__ atom_c_off, int nvec) {
+  const int atom = blockIdx.x, r = blockIdx.y;
+  const int v = blockIdx.z * blockDim.x + threadIdx.x;
+  if (r >= 2 * atom_npj[atom] || v >= nvec) return;
+  cplx<T> acc = cmake<cplx<T>>(0, 0);
+  for (int k = chunk_off[atom]; k < chunk_off[atom + 1]; ++k) {
+    const cplx<T> p = Cpart[((size_t)k * 2 * MAXPJ + r) * nvec + v];
+    acc.x += p.x;
+    acc.y += p.y;
+  }
+  Cbuf[(size_t)(atom_c_off[atom] + r) * nvec + v] = acc;
 }
 
 // Cp[(c_off + r) * nvec + v] = sum_c Delta[r][c] C[(c_off + c) * nvec + v]
@@ -177,10 +199,23 @@ cudaError_t run_project(gbc_ctx* c, const cplx<T>* X, int nvec, int ldx, cplx<T>
   const ProjDev& pj = c->proj;
   const cplx<T>* P = std::is_same<T, double>::value ? (const cplx<T>*)pj.d_P64
                                                     : (const cplx<T>*)pj.d_P32;
+  // deterministic mode: per-chunk sums, then each atom's chunks added in order
+  cplx<T>* Cpart = nullptr;
+  if (c->deterministic) {
+    if (gbc_ensure_work(c, 11, sizeof(cplx<T>) * pj.nchunks * 2 * MAXPJ * (size_t)nvec) != GBC_OK)
+      return cudaErrorMemoryAllocation;
+    Cpart = (cplx<T>*)c->work[11];
+  }
   dim3 grid(pj.nchunks, (2 * nvec + kCols - 1) / kCols);
   nl_project<T, MAXPJ><<<grid, kCols, 0, s>>>(X, ldx, nvec, pj.d_chunks, pj.d_nodes, P,
                                               pj.d_atom_npj, pj.d_atom_pv_off, pj.d_atom_c_off,
-                                              Cbuf, c->mesh.M);
+                                              Cbuf, c->mesh.M, Cpart);
+  if (!Cpart) return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 g2(pj.natoms, 2 * pj.max_npj, (nvec + kCols - 1) / kCols);
+  k_nl_chunk_sum<T, MAXPJ><<<g2, kCols, 0, s>>>(Cpart, Cbuf, pj.d_chunk_off, pj.d_atom_npj,
+                                                pj.d_atom_c_off, nvec);
   return cudaGetLastError();
 }
 

@@ -153,7 +153,8 @@ __global__ void k_mass(const MeshDev m, const double* mx, const double* my, cons
   invmd32[I] = (float)(1.0 / v);
 }
 
-// fields[e][c][q] = w_q J * {V + |k|^2/2, bx, by, bz}[e][q]
+// fields[e][c][q] = w_q J * {V + |k|^2/2, bx, by, bz}[e][q] (FP64); the FP32 copy is
+// [e][q][c], one float4 per quadrature point
 __global__ void k_fields(const double* raw, long long E, int nq, double jac, double k2half,
                          const double* __restrict__ wq, double* f64, float* f32) {
   const long long nq3 = (long long)nq * nq * nq;
@@ -168,7 +169,7 @@ __global__ void k_fields(const double* raw, long long E, int nq, double jac, dou
     if (c == 0) val += k2half;
     const double o = w * val;
     f64[(e * 4 + c) * nq3 + q] = o;
-    f32[(e * 4 + c) * nq3 + q] = (float)o;
+    f32[(e * nq3 + q) * 4 + c] = (float)o;   // FP32: one float4 per point
   }
 }
 
@@ -289,9 +290,15 @@ __global__ void k_passemble(const PTab t, const double* __restrict__ pvals,
                             const int* __restrict__ entry_atom, const long long* __restrict__ entry_pos,
                             const long long* __restrict__ entry_pv_base,
                             const int* __restrict__ atom_npj, const int* __restrict__ atom_pv_off,
-                            double2* P) {
+                            double2* P, const int* __restrict__ ent_off, int round) {
   extern __shared__ double2 f[];
-  const long long ent = blockIdx.x;
+  // one launch over every support entry, or (ent_off set: deterministic assembly) the
+  // round-th entry of every atom, so that no two blocks of a launch add to one value
+  long long ent = blockIdx.x;
+  if (ent_off) {
+    ent = (long long)ent_off[blockIdx.x] + round;
+    if (ent >= ent_off[blockIdx.x + 1]) return;
+  }
   const int chi = blockIdx.y;
   const int atom = entry_atom[ent];
   const int npj = atom_npj[atom];
@@ -379,17 +386,41 @@ gbc_status setup_projectors(gbc_ctx* c) {
   }
   long long* dbase = nullptr;
   GBC_TRY(upload(c, (void**)&dbase, base.data(), sizeof(long long) * base.size()));
-  dim3 grid((unsigned)pj.nentries, pj.max_npj);
   const size_t smem = sizeof(double2) * nq * nq * nq;
-  k_passemble<<<grid, 128, smem>>>(t, pj.d_pvals, pj.d_entry_cell, pj.d_entry_img,
-                                   pj.d_entry_atom, pj.d_entry_pos, dbase, pj.d_atom_npj,
-                                   pj.d_atom_pv_off, pj.d_P64);
-  GBC_CU(c, cudaGetLastError());
+  int* dent = nullptr;
+  if (!c->deterministic) {
+    dim3 grid((unsigned)pj.nentries, pj.max_npj);
+    k_passemble<<<grid, 128, smem>>>(t, pj.d_pvals, pj.d_entry_cell, pj.d_entry_img,
+                                     pj.d_entry_atom, pj.d_entry_pos, dbase, pj.d_atom_npj,
+                                     pj.d_atom_pv_off, pj.d_P64, nullptr, 0);
+    GBC_CU(c, cudaGetLastError());
+  } else {
+    // deterministic: round r adds the r-th support entry of every atom (atoms write
+    // disjoint tables), so each value receives its terms in entry order
+    std::vector<int> eatom(pj.nentries), eoff(pj.natoms + 1, 0);
+    GBC_CU(c, cudaMemcpy(eatom.data(), pj.d_entry_atom, sizeof(int) * pj.nentries,
+                         cudaMemcpyDeviceToHost));
+    for (int a : eatom) ++eoff[a + 1];
+    int rounds = 0;
+    for (int a = 0; a < pj.natoms; ++a) {
+      rounds = std::max(rounds, eoff[a + 1]);
+      eoff[a + 1] += eoff[a];
+    }
+    GBC_TRY(upload(c, (void**)&dent, eoff.data(), sizeof(int) * eoff.size()));
+    dim3 grid((unsigned)pj.natoms, pj.max_npj);
+    for (int r = 0; r < rounds; ++r) {
+      k_passemble<<<grid, 128, smem>>>(t, pj.d_pvals, pj.d_entry_cell, pj.d_entry_img,
+                                       pj.d_entry_atom, pj.d_entry_pos, dbase, pj.d_atom_npj,
+                                       pj.d_atom_pv_off, pj.d_P64, dent, r);
+      GBC_CU(c, cudaGetLastError());
+    }
+  }
   k_to_f32<<<(unsigned)((ntab + 2 + 255) / 256), 256>>>(pj.d_P64, pj.d_P32, ntab + 2);
   GBC_CU(c, cudaGetLastError());
   GBC_CU(c, tc_expand_prepare(pj, 0));
   GBC_CU(c, cudaDeviceSynchronize());
   cudaFree(dbase);
+  cudaFree(dent);
   return GBC_OK;
 }
 
@@ -599,6 +630,12 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
   GBC_TRY(upload(c, (void**)&pj.d_delta64, delta, sizeof(double2) * pj.delta_off[natoms]));
   GBC_TRY(upload(c, (void**)&pj.d_delta32, d32.data(), sizeof(float2) * d32.size()));
   GBC_TRY(upload(c, (void**)&pj.d_chunks, chunks.data(), sizeof(int4) * chunks.size()));
+  {
+    std::vector<int> coff(natoms + 1, 0);
+    for (const int4& q : chunks) ++coff[q.x + 1];
+    for (int a = 0; a < natoms; ++a) coff[a + 1] += coff[a];
+    GBC_TRY(upload(c, (void**)&pj.d_chunk_off, coff.data(), sizeof(int) * coff.size()));
+  }
   GBC_TRY(upload(c, (void**)&pj.d_own_node, onode.data(), sizeof(long long) * onode.size()));
   GBC_TRY(upload(c, (void**)&pj.d_own_pos, opos.data(), sizeof(int) * opos.size()));
   GBC_TRY(upload(c, (void**)&pj.d_own_xptr, oxptr.data(), sizeof(int) * oxptr.size()));
@@ -633,7 +670,7 @@ void free_projectors(ProjDev& pj) {
                   pj.d_delta32, pj.d_chunks, pj.d_own_node, pj.d_own_pos, pj.d_own_xptr,
                   pj.d_own_xinc, pj.d_exp_chunks, pj.d_tcexp_chunks, pj.d_tcexp_slots,
                   pj.d_pvals, pj.d_entry_cell, pj.d_entry_img, pj.d_entry_atom, pj.d_entry_pos,
-                  pj.d_xA};
+                  pj.d_xA, pj.d_chunk_off};
   for (void* p : ptrs) cudaFree(p);
   pj = ProjDev();
 }

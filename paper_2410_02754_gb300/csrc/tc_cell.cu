@@ -266,7 +266,7 @@ __global__ void k_tcl_point(const float* __restrict__ U, const float* __restrict
     float ou_r = 0.f, ou_i = 0.f, od_r = 0.f, od_i = 0.f;
     if (q < nq3) {
       const float* f = fields + (size_t)(cell0 + c) * 4 * nq3;
-      const float V = f[q], bx = f[nq3 + q], by = f[2 * nq3 + q], bz = f[3 * nq3 + q];
+      const float V = f[4 * q], bx = f[4 * q + 1], by = f[4 * q + 2], bz = f[4 * q + 3];
       const float ur = U[r_u * QP + q], ui = U[(r_u + 1) * QP + q];
       const float dr = U[r_d * QP + q], di = U[(r_d + 1) * QP + q];
       // [(V + bz) u + (bx - i by) d ; (bx + i by) u + (V - bz) d]

@@ -38,7 +38,8 @@ EXPORTS = ["gbc_create", "gbc_destroy", "gbc_last_error", "gbc_version", "gbc_se
            "gbc_sync_status", "gbc_density", "gbc_density_dev", "gbc_fermi_occupations",
            "gbc_prolongate", "gbc_scf_fields", "gbc_anderson_mix", "gbc_get_ndof",
            "gbc_filter_backward", "gbc_alu_peak", "gbc_set_cell_variant",
-           "gbc_get_cell_variant", "gbc_build_info", "gbc_check_selftest"]
+           "gbc_get_cell_variant", "gbc_build_info", "gbc_check_selftest",
+           "gbc_set_deterministic", "gbc_get_deterministic"]
 FAMILIES = {"hx_local": 0, "nonlocal": 1, "cheb": 2, "gram": 3, "rotate": 4, "dense": 5}
 
 
@@ -103,6 +104,8 @@ def load_library(path: str = LIB_PATH):
         "gbc_tc_gemm_nt": ([V, V, V, I, I, I, V], I),
         "gbc_tc_wait_selftest": ([I, V], I),
         "gbc_build_info": ([IP], I),
+        "gbc_set_deterministic": ([P, I], I),
+        "gbc_get_deterministic": ([P, IP], I),
         "gbc_check_selftest": ([ct.c_longlong, V], I),
         "gbc_set_nonlocal_engine": ([P, I], I),
         "gbc_get_nonlocal_engine": ([P, IP], I),
@@ -232,6 +235,15 @@ class Context:
     def set_precision(self, prec):
         self._chk(self.lib.gbc_set_precision(self.h, int(prec)))
         self.prec = prec
+
+    def set_deterministic(self, on=True):
+        """Fixed-order sums instead of atomics in the FP64 kernels (gbc_set_deterministic)."""
+        self._chk(self.lib.gbc_set_deterministic(self.h, 1 if on else 0))
+
+    def deterministic(self):
+        v = ct.c_int()
+        self._chk(self.lib.gbc_get_deterministic(self.h, ct.byref(v)))
+        return bool(v.value)
 
     def set_nonlocal_engine(self, engine):
         """0 = SIMT cores, 1 = tcgen05 tensor cores (FP32 projector contractions)."""
