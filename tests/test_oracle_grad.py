@@ -100,3 +100,41 @@ def test_planted_adjoint_mistake_is_caught(setup, monkeypatch):
     gdx = 0.0   # the direct term has no X0 dependence beyond Y
     ana_wrong = float(np.real(np.sum(wrong.conj() * D))) + gdx
     assert abs(num - ana_wrong) > 1e-3 * abs(num)
+
+
+def test_fifty_joint_directions_fourth_order(setup):
+    """50 seeded joint directions (V_eff, B_x, B_y, B_z at every quadrature point, every
+    Hermitian Delta_a, the input block X0 -- all perturbed together): the gradient's
+    directional derivative agrees with the fourth-order central difference
+    (8 (L(h) - L(-h)) - (L(2h) - L(-2h))) / 12h to 1e-7 relative.  The loss is a
+    polynomial in the parameters, so the O(h^4) truncation at h = 1e-3 is far below the
+    bound and rounding contributes ~eps |L| / h."""
+    prob, X0, w, L, gX, g, gD, rng = setup
+    rng = np.random.default_rng(2024)
+    names = ["veff", "bx", "by", "bz"]
+    base = [np.array(getattr(prob, n)) for n in names]
+    worst = 0.0
+    for trial in range(50):
+        df = [rng.normal(size=b.shape) for b in base]
+        E = []
+        for a in prob.atoms:
+            n = a.delta.shape[0]
+            B = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+            E.append(0.5 * (B + B.conj().T))
+        D = rng.normal(size=X0.shape) + 1j * rng.normal(size=X0.shape)
+
+        def f(h):
+            atoms = [syn.Atom(x.pos, x.npj, x.supp_cell, x.supp_img, x.pvals, x.delta + h * E[i])
+                     for i, x in enumerate(prob.atoms)]
+            p = prob.with_(atoms=atoms, **{n: b + h * d for n, b, d in zip(names, base, df)})
+            return og.total_loss(fe.Discretisation(p), X0 + h * D, w, M_DEG, LT, LMAX, LMIN)
+
+        h = 1e-3
+        num = (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h)
+        ana = (sum(float(np.sum(g[:, c] * df[c])) for c in range(4))
+               + sum(float(np.real(np.sum(gD[a].conj() * E[a]))) for a in range(len(E)))
+               + float(np.real(np.sum(gX.conj() * D))))
+        err = abs(num - ana) / max(abs(num), 1e-3 * abs(L))
+        worst = max(worst, err)
+    print(f"  PIN-10: 50 joint directions, worst relative error {worst:.2e}")
+    assert worst <= 1e-7, worst
