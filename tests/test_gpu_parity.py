@@ -106,6 +106,43 @@ def test_errors_are_reported(g):
     ctx.close()
 
 
+def test_c1_full_size_256_vectors_bench_path(g):
+    """The bench's own launch configuration at full size: cube16_p6 (k != 0), 256 vectors
+    FP32, the context tuned as the bench tunes it (cell-apply variant, nonlocal engine), so
+    H.X runs the tuned counter-scheduled cell kernel and the TMA-fed projection, and the
+    first filter step runs the fused recurrence (expansion from packed operands, cell
+    interior rows finished in the cell kernel, face-row pass).  Sampled rows against the
+    oracle: (H X)[rows], and X_1[rows] = (M_D^-1 (H X)[rows] - c X[rows]) / (lmin - c) of a
+    degree-1 filter (Eq. chebfilt with sigma_1 = e / (lmin - c))."""
+    prob = syn.config("cube16_p6", kindex=1)
+    d = fe.Discretisation(prob)
+    M = d.mesh.nnodes
+    rng = np.random.default_rng(7)
+    rows = np.unique(rng.integers(0, M, 24))
+    X = syn.random_block(M, 256, 5)
+    ref = d.apply_h_rows(X, rows)
+    ctx = make_ctx(g, prob, 1)
+    ctx.tune(256)
+    ctx.set_nonlocal_engine(1)          # the engine the bench's tuning picks at this size
+    assert ctx.nonlocal_engine() == 1
+    Xd = to_dev(X, 1)
+    Yd = torch.empty_like(Xd)
+    ctx.apply_h(Xd, Yd)
+    ctx.sync_status()
+    idx = torch.from_numpy(rows).cuda()
+    got = Yd[idx].cpu().numpy()
+    assert rel(got, ref) < 1e-5, rel(got, ref)
+    del Yd
+    lT, lmax, lmin = 5.0, 120.0, -2.0
+    c = 0.5 * (lmax + lT)
+    ref1 = (ref / d.md[rows][:, None, None] - c * X[rows]) / (lmin - c)
+    ctx.filter(Xd, 1, lT, lmax, lmin)
+    ctx.sync_status()
+    got1 = Xd[idx].cpu().numpy()
+    assert rel(got1, ref1) < 1e-5, rel(got1, ref1)
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
 def test_filter_matches_oracle(g, prec, tol):
     prob = syn.make_problem(ncell=(3, 2, 2), h=(1.1, 1.1, 1.1), p=4, k=(0.1, 0.2, -0.1),
