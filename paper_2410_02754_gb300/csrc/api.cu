@@ -202,7 +202,8 @@ gbc_status filter_t(gbc_ctx* c, cplx<T>* X, int nvec, int ldx, int m, double lT,
       GBC_CU(c, launch_cell_f32(&j, 1, c->cell_var, s));
     }
     TimerScope ts(c, FAM_CHEB, s);
-    GBC_CU(c, launch_cheb_rows<T>(Y, cur, prev, out, invmd, c->d_face_rows, c->nface, c->mesh.M, nvec, ldx,
+    GBC_CU(c, launch_cheb_rows<T>(Y, cur, prev, out, invmd, c->d_face_rows, c->nface,
+                                  c->proj.natoms > 0 ? c->nface_supp : 0, c->mesh.M, nvec, ldx,
                                   a, cc, b, s));
   }
   if (m & 1) GBC_CU(c, launch_copy_block<T>(W, X, c->mesh.M, nvec, ldx, s));

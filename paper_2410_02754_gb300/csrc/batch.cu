@@ -360,6 +360,7 @@ gbc_status record_filters(gbc_batch* b, std::vector<SysRun>& runs, cudaStream_t 
           step(r, &cur, &prev, &out, &a, &bb);
           ChebRowsJob& j = cb.job[cb.njobs++];
           j = ChebRowsJob{r.Y, cur, prev, out, r.c->d_invmd32, r.c->d_face_rows, cb.total, r.c->mesh.M,
+                          r.c->proj.natoms > 0 ? r.c->nface_supp : 0,
                           r.nvec, r.ldx, a, r.cc, bb};
           cb.total += r.c->nface * 2LL * r.nvec;
         }

@@ -485,12 +485,14 @@ inline unsigned grid_for(long long n, int threads = 256) {
 }  // namespace
 
 // Recurrence update on the listed node rows only (the rows the fused cell
-// apply leaves to atomics: nodes on cell faces), Y zeroed there for the next step.
+// apply leaves to atomics: nodes on cell faces), Y zeroed there for the next step
+// except on the first nkeep listed rows, which the next step's nonlocal expansion
+// overwrites (rows in some atom's support).
 template <typename T>
 __global__ void k_cheb_rows(cplx<T>* __restrict__ Y, const cplx<T>* Xcur, const cplx<T>* Xprev,
                             cplx<T>* Xout, const T* __restrict__ invmd,
-                            const long long* __restrict__ rows, long long nrows, long long M,
-                            int nvec, int ldx, T a, T cshift, T b) {
+                            const long long* __restrict__ rows, long long nrows, long long nkeep,
+                            long long M, int nvec, int ldx, T a, T cshift, T b) {
   const long long n = nrows * 2 * (long long)nvec;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -511,26 +513,29 @@ __global__ void k_cheb_rows(cplx<T>* __restrict__ Y, const cplx<T>* Xcur, const 
       out.y -= b * xp.y;
     }
     Xout[o] = out;
-    Y[o] = cmake<cplx<T>>(0, 0);
+    if ((rs >> 1) >= nkeep) Y[o] = cmake<cplx<T>>(0, 0);   // rows below nkeep: overwritten next step
   }
 }
 
 template <typename T>
 cudaError_t launch_cheb_rows(cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev, cplx<T>* Xout,
-                             const T* invmd, const long long* rows, long long nrows, long long M,
-                             int nvec, int ldx, double a, double cshift, double b, cudaStream_t s) {
+                             const T* invmd, const long long* rows, long long nrows, long long nkeep,
+                             long long M, int nvec, int ldx, double a, double cshift, double b,
+                             cudaStream_t s) {
   if (nrows <= 0 || nvec <= 0) return cudaSuccess;
   k_cheb_rows<T><<<grid_for(nrows * 2 * nvec), 256, 0, s>>>(Y, Xcur, Xprev, Xout, invmd, rows,
-                                                            nrows, M, nvec, ldx, (T)a, (T)cshift,
-                                                            (T)b);
+                                                            nrows, nkeep, M, nvec, ldx, (T)a,
+                                                            (T)cshift, (T)b);
   return cudaGetLastError();
 }
 template cudaError_t launch_cheb_rows<float>(float2*, const float2*, const float2*, float2*,
                                              const float*, const long long*, long long, long long,
-                                             int, int, double, double, double, cudaStream_t);
+                                             long long, int, int, double, double, double,
+                                             cudaStream_t);
 template cudaError_t launch_cheb_rows<double>(double2*, const double2*, const double2*, double2*,
                                               const double*, const long long*, long long, long long,
-                                              int, int, double, double, double, cudaStream_t);
+                                              long long, int, int, double, double, double,
+                                              cudaStream_t);
 
 // launch_cheb_rows over several systems in one launch (batched filter)
 template <typename T>
@@ -561,7 +566,7 @@ __global__ void k_cheb_rows_batch(const __grid_constant__ ChebRowsBatch b) {
       out.y -= bb * xp.y;
     }
     ((cplx<T>*)j.Xout)[o] = out;
-    Y[o] = cmake<cplx<T>>(0, 0);
+    if ((rs >> 1) >= j.nkeep) Y[o] = cmake<cplx<T>>(0, 0);
   }
 }
 

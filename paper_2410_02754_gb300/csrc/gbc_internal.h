@@ -220,7 +220,8 @@ struct gbc_ctx {
   int vb32 = 2;                      // FP64 kernel tile (vectors per CTA; fixed)
   int cell_var = 0;                  // FP32 cell-apply variant (GBC_CELL_VARIANTS), set by the tuner
   long long nface = 0;               // free nodes on cell faces (shared by several cells)
-  long long* d_face_rows = nullptr;  // [nface] their node indices, ascending
+  long long* d_face_rows = nullptr;  // [nface] their node indices: support rows first
+  long long nface_supp = 0;          // leading rows of d_face_rows in some atom's support
   int nl_engine = 1;                 // FP32 projector contractions: 0 SIMT, 1 tensor cores
   TclState* tcl = nullptr;           // GBC_TF32 / GBC_BF16X3 cell apply (built on first use)
   // optional per-kernel-family timing (gbc_set_timing)
@@ -357,9 +358,12 @@ cudaError_t launch_cheb_step(const cplx<T>* Y, const cplx<T>* Xcur, const cplx<T
 // the same update restricted to the listed rows (node indices), Y zeroed there
 template <typename T>
 cudaError_t launch_cheb_rows(cplx<T>* Y, const cplx<T>* Xcur, const cplx<T>* Xprev, cplx<T>* Xout,
-                             const T* invmd, const long long* rows, long long nrows, long long M,
-                             int nvec, int ldx, double a, double cshift, double b, cudaStream_t s);
-gbc_status setup_face_rows(gbc_ctx* c);
+                             const T* invmd, const long long* rows, long long nrows, long long nkeep,
+                             long long M, int nvec, int ldx, double a, double cshift, double b,
+                             cudaStream_t s);
+// the cell-face rows (nodes on a cell face); with insupp ([M], 1 = in some atom's
+// support) those rows come first and their count is c->nface_supp
+gbc_status setup_face_rows(gbc_ctx* c, const std::vector<char>* insupp = nullptr);
 #define GBC_MAX_CHEB_BATCH 32
 // the row update of several systems in one launch
 struct ChebRowsJob {
@@ -371,6 +375,7 @@ struct ChebRowsJob {
   const long long* rows;
   long long start;     // first flat element (listed row x spin x vector) of this job
   long long M;         // nodes of the system (the rows' bound)
+  long long nkeep;     // listed rows below this are not zeroed (overwritten next step)
   int nvec, ldx;
   double a, c, b;
 };

@@ -839,8 +839,10 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
       int use = 0;
       int held0 = -1, held1 = -1;   // slot instance whose A block each stage holds
       bool ok = true;
+      int4 chn_next = blockIdx.x < nchunks ? chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
       for (int chn = blockIdx.x; chn < nchunks && ok && !*abort_flag; chn += gridDim.x) {
-        const int4 ch = chunks[chn];
+        const int4 ch = chn_next;
+        if (chn + (int)gridDim.x < nchunks) chn_next = chunks[chn + gridDim.x];   // in flight over this chunk
         for (int j = 0; j < ntiles && ok; ++j) {
           for (int sl = 0; sl < ch.w; ++sl, ++use) {
             const int st = use & 1;
@@ -908,9 +910,11 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
     const uint32_t myrow_s = tc::smem_u32(myrow);
     int n = 0;
     bool ok = true;
+    int4 chn_next = blockIdx.x < nchunks ? chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
     for (int chn = blockIdx.x; chn < nchunks && ok; chn += gridDim.x) {
-      const int4 ch = chunks[chn];
+      const int4 ch = chn_next;
       long long node = r < ch.y ? own_node[ch.x + r] : -1;
+      if (chn + (int)gridDim.x < nchunks) chn_next = chunks[chn + gridDim.x];
       if (node >= 0 && !GBC_IN_RANGE(GBC_SITE_NL_NODE, node, M)) node = -1;   // checked build
       for (int j = 0; j < ntiles; ++j, ++n) {
         const int acc = n & 1;
@@ -925,14 +929,11 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
         float4* dst = reinterpret_cast<float4*>(myrow);
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
-          float v[64];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float t[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * acc + 64 * h + 16 * c), t);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) v[16 * c + e] = t[e];
-          }
+          uint32_t v[64];   // both loads in flight, one wait
+          const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * acc + 64 * h);
+          tc::tmem_ld32_nowait(ta, v);
+          tc::tmem_ld32_nowait(ta + 32, v + 32);
+          tc::tmem_wait_ld();
           if (h == 1) {   // accumulator read: hand it back to the MMA thread
             tc::fence_before_sync();
             __syncwarp();
@@ -941,7 +942,8 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
           if (node >= 0) {
 #pragma unroll
             for (int e = 0; e < 16; ++e)
-              dst[16 * h + e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+              dst[16 * h + e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                            __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
           }
         }
         if (node >= 0) {

@@ -224,7 +224,7 @@ gbc_status setup_mass(gbc_ctx* c) {
 // Free nodes on a cell face (a local index 0 or p in some direction): the rows
 // several cells add to.  In direction d the free index f is the global node
 // index g (periodic) or g - 1 (Dirichlet), and the node is on a face iff g % p == 0.
-gbc_status setup_face_rows(gbc_ctx* c) {
+gbc_status setup_face_rows(gbc_ctx* c, const std::vector<char>* insupp) {
   const MeshDev& m = c->mesh;
   std::vector<char> face[3];
   for (int d = 0; d < 3; ++d) {
@@ -241,6 +241,14 @@ gbc_status setup_face_rows(gbc_ctx* c) {
       for (int x = 0; x < m.nfree[0]; ++x)
         if (face[0][x] || face[1][y] || face[2][z])
           rows.push_back(((long long)z * m.nfree[1] + y) * m.nfree[0] + x);
+  // rows in some atom's support first (each ascending): the fused filter's expansion
+  // overwrites those rows every step, so the face-row pass need not zero them
+  c->nface_supp = 0;
+  if (insupp) {
+    auto mid = std::stable_partition(rows.begin(), rows.end(),
+                                     [&](long long r) { return (*insupp)[(size_t)r] != 0; });
+    c->nface_supp = (long long)(mid - rows.begin());
+  }
   cudaFree(c->d_face_rows);
   c->d_face_rows = nullptr;
   c->nface = (long long)rows.size();
@@ -614,6 +622,11 @@ gbc_status build_projector_structure(gbc_ctx* c, int natoms, const int* npj, con
     }
   }
   if (oxinc.empty()) oxinc.push_back(make_int2(0, 0));   // keep a valid allocation
+  {
+    std::vector<char> insupp((size_t)m.M, 0);
+    for (long long I : onode) insupp[(size_t)I] = 1;
+    GBC_TRY(setup_face_rows(c, &insupp));
+  }
   pj.nuniq = (long long)onode.size();
   pj.nexp_chunks = (int)echunks.size();
 
