@@ -327,10 +327,12 @@ size_t nl_work_bytes(const gbc_ctx* c, int nvec, int ldx, size_t el, size_t* bpr
 bool tc_nonlocal_supported(const ProjDev& pj);
 cudaError_t launch_tc_project(const ProjDev& pj, long long M, const float2* X, int nvec, int ldx,
                               float2* Cbuf, cudaStream_t s);
-// overwrite with bpre (tc_expand_bpre_bytes of device scratch, 256-byte aligned): the
-// expansion from packed operands; otherwise the operand-staging kernel
+// overwrite with bpre (tc_expand_bpre_bytes of device scratch, 256-byte aligned) and ctr
+// (a work counter, zeroed here on s): the expansion from packed operands; otherwise the
+// operand-staging kernel
 cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, const float2* Cp,
-                             cudaStream_t s, bool overwrite = false, void* bpre = nullptr);
+                             cudaStream_t s, bool overwrite = false, void* bpre = nullptr,
+                             unsigned long long* ctr = nullptr);
 // scratch bytes of the packed expansion's B blocks for an nvec-vector block (0: not used)
 size_t tc_expand_bpre_bytes(const ProjDev& pj, int nvec, int ldx);
 // pack the expansion's A blocks from the FP32 P tables (allocates them once per projector set)

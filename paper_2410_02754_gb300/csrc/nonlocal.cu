@@ -239,7 +239,7 @@ cudaError_t launch_nonlocal(gbc_ctx* c, const cplx<T>* X, cplx<T>* Y, int nvec, 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if constexpr (std::is_same<T, float>::value) {
-    if (use_tc(c)) return launch_tc_expand(pj, Y, nvec, ldx, Cpbuf, s, overwrite, bpre);
+    if (use_tc(c)) return launch_tc_expand(pj, Y, nvec, ldx, Cpbuf, s, overwrite, bpre, c->d_cell_ctr);
   }
   const cplx<T>* P = std::is_same<T, double>::value ? (const cplx<T>*)pj.d_P64
                                                     : (const cplx<T>*)pj.d_P32;

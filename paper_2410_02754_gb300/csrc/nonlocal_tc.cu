@@ -702,7 +702,8 @@ constexpr int kXRow = 128 * 4 + 16;               // epilogue row: one tile row 
 constexpr int kXThreads = 192;                    // producer, MMA, 4 epilogue warps
 
 // 256-byte alignment (the 32-byte swizzle atom), two stages, 128 staging rows, barriers
-constexpr size_t xexp_smem() { return 256 + 2 * (size_t)kXStage + 128 * (size_t)kXRow + 128; }
+// and the chunk-index ring
+constexpr size_t xexp_smem() { return 256 + 2 * (size_t)kXStage + 128 * (size_t)kXRow + 256; }
 
 // store the hi / lo split of K values v[0..kXK) of row r into an operand block
 __device__ __forceinline__ void xpack_row(float* blk, int r, const float (&v)[kXK]) {
@@ -788,8 +789,9 @@ __device__ __forceinline__ bool wait_one(uint32_t mbar, uint32_t parity, volatil
   return false;
 }
 
-// Y rows of the owned nodes = P C' (overwrite), persistent: CTA b takes the chunks
-// b, b + gridDim.x, ... and every column tile of each in turn:
+// Y rows of the owned nodes = P C' (overwrite), persistent: the CTAs take chunks from the
+// zeroed counter *ctr (one thread fetches, a four-entry ring in shared memory hands each
+// index to the MMA thread and the epilogue warps), and every column tile of each in turn:
 //   warp 0    one thread: bulk copies of each slot's A and B blocks into a two-stage ring;
 //             an A block already held by the stage (chunks of one or two atoms, from the
 //             previous tile) is not copied again
@@ -801,19 +803,23 @@ __global__ void __launch_bounds__(kXThreads, 1)
 k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int nchunks,
                const int4* __restrict__ chunks, const int* __restrict__ slots,
                const long long* __restrict__ own_node, const float* __restrict__ Apre,
-               const float* __restrict__ Bpre) {
+               const float* __restrict__ Bpre, unsigned long long* __restrict__ ctr) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 255) & ~(uintptr_t)255;
   unsigned char* stage0 = reinterpret_cast<unsigned char*>(base);
   unsigned char* rows = stage0 + 2 * kXStage;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(rows + 128 * kXRow);   // full[2] empty[2] tfull[2] tempty[2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 8);
+  // full[2] empty[2] tfull[2] tempty[2] cfull[4] cempty[4]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rows + 128 * kXRow);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   int* prog = reinterpret_cast<int*>(tslot + 2);   // [0] stage uses issued, [1] consumed, [2] commits
+  volatile int* s_chunk = reinterpret_cast<volatile int*>(prog + 3);   // [4] chunk-index ring
   auto full = [&](int s) { return tc::smem_u32(bars + s); };
   auto empty = [&](int s) { return tc::smem_u32(bars + 2 + s); };
   auto tfull = [&](int a) { return tc::smem_u32(bars + 4 + a); };
   auto tempty = [&](int a) { return tc::smem_u32(bars + 6 + a); };
+  auto cfull = [&](int k) { return tc::smem_u32(bars + 8 + k); };
+  auto cempty = [&](int k) { return tc::smem_u32(bars + 12 + k); };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // an earlier CTA gave up (read once, the same decision in every thread)
@@ -821,6 +827,8 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
   if (threadIdx.x == 0) {
     for (int i = 0; i < 6; ++i) tc::mbar_init(tc::smem_u32(bars + i), 1);
     for (int i = 6; i < 8; ++i) tc::mbar_init(tc::smem_u32(bars + i), 4);   // one per epilogue warp
+    for (int i = 8; i < 12; ++i) tc::mbar_init(tc::smem_u32(bars + i), 1);  // producer
+    for (int i = 12; i < 16; ++i) tc::mbar_init(tc::smem_u32(bars + i), 5); // MMA + 4 epilogue warps
     *abort_flag = 0;
     prog[0] = prog[1] = prog[2] = 0;
     tc::fence_mbar_init();
@@ -839,10 +847,16 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
       int use = 0;
       int held0 = -1, held1 = -1;   // slot instance whose A block each stage holds
       bool ok = true;
-      int4 chn_next = blockIdx.x < nchunks ? chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
-      for (int chn = blockIdx.x; chn < nchunks && ok && !*abort_flag; chn += gridDim.x) {
-        const int4 ch = chn_next;
-        if (chn + (int)gridDim.x < nchunks) chn_next = chunks[chn + gridDim.x];   // in flight over this chunk
+      int chn = (int)atomicAdd(ctr, 1ULL);
+      for (int kk = 0; ok && !*abort_flag; ++kk) {
+        // hand the chunk index to the other roles (nchunks or more: the end)
+        const int rs = kk & 3;
+        if (kk >= 4 && !wait_one(cempty(rs), ((kk >> 2) - 1) & 1, abort_flag)) break;
+        s_chunk[rs] = chn;
+        tc::mbar_arrive(cfull(rs));
+        if (chn >= nchunks) break;
+        const int4 ch = chunks[chn];
+        chn = (int)atomicAdd(ctr, 1ULL);   // the next index, fetched while this chunk runs
         for (int j = 0; j < ntiles && ok; ++j) {
           for (int sl = 0; sl < ch.w; ++sl, ++use) {
             const int st = use & 1;
@@ -868,7 +882,13 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
       constexpr uint32_t idesc = tc::idesc_tf32(128, 128);
       int use = 0, n = 0;
       bool ok = true;
-      for (int chn = blockIdx.x; chn < nchunks && ok && !*abort_flag; chn += gridDim.x)
+      for (int kk = 0; ok && !*abort_flag; ++kk) {
+        const int rs = kk & 3;
+        if (!wait_one(cfull(rs), (kk >> 2) & 1, abort_flag)) break;
+        const int chn = s_chunk[rs];
+        tc::mbar_arrive(cempty(rs));
+        if (chn >= nchunks) break;
+        const int4 ch = chunks[chn];
       for (int j = 0; j < ntiles && ok; ++j, ++n) {
         const int acc = n & 1;
         if (n >= 2 && !wait_one(tempty(acc), ((n >> 1) - 1) & 1, abort_flag)) {
@@ -876,7 +896,6 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
           break;
         }
         tc::fence_after_sync();
-        const int4 ch = chunks[chn];
         const uint32_t d = tmem + (uint32_t)(128 * acc);
         for (int sl = 0; sl < ch.w; ++sl, ++use) {
           const int st = use & 1;
@@ -901,6 +920,7 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
         tc::mma_commit(tfull(acc));
         prog[2] = n + 1;
       }
+      }
     }
   } else {
     // epilogue: thread -> row r of the accumulator (TMEM lane r)
@@ -910,11 +930,15 @@ k_tc_expand_ws(float* __restrict__ Yr, long long M, int ncols, int ntiles, int n
     const uint32_t myrow_s = tc::smem_u32(myrow);
     int n = 0;
     bool ok = true;
-    int4 chn_next = blockIdx.x < nchunks ? chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
-    for (int chn = blockIdx.x; chn < nchunks && ok; chn += gridDim.x) {
-      const int4 ch = chn_next;
+    for (int kk = 0; ok; ++kk) {
+      const int rs = kk & 3;
+      if (!wait_uniform(cfull(rs), (kk >> 2) & 1, abort_flag)) break;
+      const int chn = s_chunk[rs];
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(cempty(rs));
+      if (chn >= nchunks) break;
+      const int4 ch = chunks[chn];
       long long node = r < ch.y ? own_node[ch.x + r] : -1;
-      if (chn + (int)gridDim.x < nchunks) chn_next = chunks[chn + gridDim.x];
       if (node >= 0 && !GBC_IN_RANGE(GBC_SITE_NL_NODE, node, M)) node = -1;   // checked build
       for (int j = 0; j < ntiles; ++j, ++n) {
         const int acc = n & 1;
@@ -1089,8 +1113,8 @@ cudaError_t tc_expand_prepare(ProjDev& pj, cudaStream_t s) {
 }
 
 cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, const float2* Cp,
-                             cudaStream_t s, bool overwrite, void* bpre) {
-  if (overwrite && bpre && tc_expand_bpre_bytes(pj, nvec, ldx) > 0) {
+                             cudaStream_t s, bool overwrite, void* bpre, unsigned long long* ctr) {
+  if (overwrite && bpre && ctr && tc_expand_bpre_bytes(pj, nvec, ldx) > 0) {
     const int ntiles = (4 * ldx + 127) / 128;
     k_xpack_b<<<dim3((unsigned)pj.natoms, (unsigned)ntiles), 128, 0, s>>>(
         reinterpret_cast<float*>(bpre), Cp, ldx, nvec, pj.d_atom_npj, pj.d_atom_c_off);
@@ -1100,9 +1124,11 @@ cudaError_t launch_tc_expand(const ProjDev& pj, float2* Y, int nvec, int ldx, co
     e = cudaFuncSetAttribute(k_tc_expand_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min(pj.ntc_exp, gbc_sm_count());
+    e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     k_tc_expand_ws<<<grid, kXThreads, smem, s>>>(reinterpret_cast<float*>(Y), pj.M, 4 * ldx, ntiles, pj.ntc_exp,
                                                  pj.d_tcexp_chunks, pj.d_tcexp_slots, pj.d_own_node,
-                                                 pj.d_xA, reinterpret_cast<const float*>(bpre));
+                                                 pj.d_xA, reinterpret_cast<const float*>(bpre), ctr);
     return cudaGetLastError();
   }
   constexpr size_t smem = expand_smem();
