@@ -290,6 +290,8 @@ def run_gpu(args):
     ctx32 = build_contexts(g, prob, ks, g.FP32, args.nl_engine)
     for c in ctx32:
         c.tune(nvec)             # FP32 cell-apply variant (cached per p, k, block size)
+        if args.cell_variant >= 0:
+            c.set_cell_variant(args.cell_variant)
     X0 = syn.random_block(M, nvec, 0)
     v0 = torch.from_numpy(syn.random_start(M, 0)).cuda()
     bounds = []
@@ -1072,6 +1074,8 @@ def main():
     ap.add_argument("--cycles", type=int, default=3, help="ChFSI cycles of the accuracy leg")
     ap.add_argument("--nl-engine", type=int, default=1, choices=[0, 1],
                     help="FP32 projector contractions: 0 SIMT cores, 1 tcgen05 tensor cores")
+    ap.add_argument("--cell-variant", type=int, default=-1,
+                    help="FP32 cell-apply variant of the main leg (profiling runs; -1: the tuner's)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -360,11 +360,12 @@ gbc_status gbc_get_tile(const gbc_ctx* ctx, int* vectors_per_cta);
  * GBC_CELL_VARIANTS - 1: 0 = 2 vectors x 256 threads with registers for 4 CTAs
  * per SM, paired FP32 multiply-adds on (re, im); 1 = the same tile with
  * registers for 3 CTAs per SM; 2 and 3 = variants 0 and 1 with scalar FP32
- * multiply-adds.  (One vector x 128 threads per CTA measured 1.5-2.5x slower at
- * p = 6 and is not compiled.)  gbc_get_cell_variant
+ * multiply-adds; 4 = 4 vectors x 512 threads with registers for 2 CTAs per SM,
+ * scalar multiply-adds.  (One vector x 128 threads per CTA measured 1.5-2.5x
+ * slower at p = 6 and is not compiled.)  gbc_get_cell_variant
  * also returns the variant's vectors and threads per CTA (either pointer may be
  * NULL).  GBC_EINVAL for a variant out of range. */
-#define GBC_CELL_VARIANTS 4
+#define GBC_CELL_VARIANTS 5
 gbc_status gbc_set_cell_variant(gbc_ctx* ctx, int variant);
 gbc_status gbc_get_cell_variant(const gbc_ctx* ctx, int* variant, int* vectors_per_cta,
                                 int* threads_per_cta);

@@ -628,8 +628,9 @@ gbc_status gbc_sync_status(gbc_ctx* c, void* stream) {
   // so all are cleared)
   using Reader = cudaError_t (*)(unsigned long long*, cudaStream_t);
   static const Reader readers[] = {gbc_check_word_cell0, gbc_check_word_cell1, gbc_check_word_cell2,
-                                   gbc_check_word_cell3, gbc_check_word_hx64,  gbc_check_word_blas,
-                                   gbc_check_word_nl,    gbc_check_word_nltc,  gbc_check_word_api};
+                                   gbc_check_word_cell3, gbc_check_word_cell4, gbc_check_word_hx64,
+                                   gbc_check_word_blas,  gbc_check_word_nl,    gbc_check_word_nltc,
+                                   gbc_check_word_api};
   unsigned long long first = 0;
   for (Reader rd : readers) {
     unsigned long long w = 0;

@@ -68,15 +68,15 @@ void tune_load() {
   FILE* fp = std::fopen(f.c_str(), "r");
   if (!fp) return;
   char line[1024];
-  static_assert(GBC_CELL_VARIANTS == 4, "the cache line format lists four variant times");
+  static_assert(GBC_CELL_VARIANTS == 5, "the cache line format lists five variant times");
   while (std::fgets(line, sizeof line, fp)) {
     char key[512];
     TuneEntry e;
     if (std::sscanf(line,
-                    " \"%511[^\"]\": {\"variant\": %d, \"nl_engine\": %d, \"ms\": [%f, %f, %f, %f], "
-                    "\"nl_ms\": [%f, %f]",
-                    key, &e.variant, &e.nl_engine, &e.ms[0], &e.ms[1], &e.ms[2], &e.ms[3], &e.nl_ms[0],
-                    &e.nl_ms[1]) >= 3 &&
+                    " \"%511[^\"]\": {\"variant\": %d, \"nl_engine\": %d, \"ms\": [%f, %f, %f, %f, "
+                    "%f], \"nl_ms\": [%f, %f]",
+                    key, &e.variant, &e.nl_engine, &e.ms[0], &e.ms[1], &e.ms[2], &e.ms[3], &e.ms[4],
+                    &e.nl_ms[0], &e.nl_ms[1]) >= 3 &&
         e.variant >= 0 && e.variant < GBC_CELL_VARIANTS)
       g_tune_cache[key] = e;
   }

@@ -64,6 +64,7 @@ cudaError_t gbc_check_word_cell0(unsigned long long* w, cudaStream_t s);
 cudaError_t gbc_check_word_cell1(unsigned long long* w, cudaStream_t s);
 cudaError_t gbc_check_word_cell2(unsigned long long* w, cudaStream_t s);
 cudaError_t gbc_check_word_cell3(unsigned long long* w, cudaStream_t s);
+cudaError_t gbc_check_word_cell4(unsigned long long* w, cudaStream_t s);
 cudaError_t gbc_check_word_hx64(unsigned long long* w, cudaStream_t s);
 cudaError_t gbc_check_word_blas(unsigned long long* w, cudaStream_t s);
 cudaError_t gbc_check_word_nl(unsigned long long* w, cudaStream_t s);

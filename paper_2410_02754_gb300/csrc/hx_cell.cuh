@@ -199,14 +199,18 @@ template <int NP> __host__ __device__ constexpr int cell_bufq() {   // points of
   return NP * (1 + CellLayout<NP>::QY + CellLayout<NP>::QZ) + 1;
 }
 
-template <int NP, int NQ> __host__ __device__ constexpr int cell_vstride() {
-  // float2 elements per vector: [A | T2 | T1], two spins per point, padded to 8 mod 16
+template <int NP, int NQ, int VB> __host__ __device__ constexpr int cell_vstride() {
+  // float2 elements per vector: [A | T2 | T1], two spins per point, padded so that the
+  // VB vectors of a lane group start in distinct quarters (VB = 4: 4 mod 16) or halves
+  // (VB = 2: 8 mod 16) of a 128-byte bank row (the same wavefront model as the strides)
+  static_assert(VB == 2 || VB == 4, "VB");
   constexpr int n = 2 * (2 * cell_bufa<NP>() + cell_bufq<NP>());
-  return n + ((24 - n % 16) % 16);
+  constexpr int r = VB == 4 ? 4 : 8;
+  return n + ((16 + r - n % 16) % 16);
 }
 // vector buffers, then the node-offset tables of the current and the next work item
 template <int NP, int NQ, int VB> constexpr size_t hx_cell_smem() {
-  return sizeof(float2) * (size_t)VB * cell_vstride<NP, NQ>() + sizeof(int) * 2 * 3 * NP + 16;
+  return sizeof(float2) * (size_t)VB * cell_vstride<NP, NQ, VB>() + sizeof(int) * 2 * 3 * NP + 16;
 }
 constexpr int kNoNode = -(1 << 29);   // offset of a direction with no free node (Dirichlet face)
 
@@ -220,7 +224,7 @@ __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int n
                                           unsigned long long* __restrict__ ctr) {
   constexpr int BA = cell_bufa<NP>();
   constexpr int NQ3 = NQ * NQ * NQ;
-  constexpr int VS = cell_vstride<NP, NQ>();
+  constexpr int VS = cell_vstride<NP, NQ, VB>();
   using L = CellLayout<NP>;
   extern __shared__ __align__(16) float2 sm[];
   // spin s of point pidx of vector v: Buf(v)[2 * pidx + s]

@@ -86,9 +86,8 @@ def test_tuner_picks_a_tile_and_keeps_parity(g):
     c.set_problem(prob)
     c.set_precision(1)
     vb = c.tune(8)
-    assert vb == 2
     var, vb2, nt = c.cell_variant()
-    assert 0 <= var < 4 and vb2 == vb and nt == 256
+    assert 0 <= var < 5 and vb2 == vb and (vb, nt) == ((4, 512) if var == 4 else (2, 256))
     X = syn.random_block(d.mesh.nnodes, 8, 3)
     Xd = torch.from_numpy(X).to(torch.complex64).cuda()
     Yd = torch.empty_like(Xd)
@@ -119,11 +118,50 @@ def test_tuner_json_cache_and_nonlocal_engine(g, tmp_path, monkeypatch):
     e = data[key[0]]
     assert e["variant"] == c.cell_variant()[0]
     assert e["nl_engine"] == c.nonlocal_engine() and e["nl_engine"] in (0, 1)
-    assert len(e["ms"]) == 4 and min(e["ms"]) > 0 and len(e["nl_ms"]) == 2
+    assert len(e["ms"]) == 5 and min(e["ms"]) > 0 and len(e["nl_ms"]) == 2
     X = syn.random_block(d.mesh.nnodes, 40, 4)
     Xd = torch.from_numpy(X).to(torch.complex64).cuda()
     Yd = torch.empty_like(Xd)
     c.apply_h(Xd, Yd)
     c.sync_status()
     assert rel(Yd.cpu().numpy(), d.apply_h(X)) < 1e-5
+    c.close()
+
+
+VARIANT_CASES = [
+    # ncell, p, k, nvec: every compiled order's largest tables at p = 6 and 7 (n_q = p + 2),
+    # vector counts that leave a ragged last chunk of 2 and of 4 vectors
+    ((2, 2, 2), 6, (0.1, -0.05, 0.2), 7),
+    ((2, 2, 2), 6, (0.0, 0.0, 0.0), 5),
+    ((3, 2, 2), 2, (0.2, 0.0, 0.0), 9),
+    ((2, 1, 2), 7, (0.0, 0.1, 0.0), 6),
+]
+
+
+@pytest.mark.parametrize("var", range(5))
+@pytest.mark.parametrize("case", VARIANT_CASES, ids=lambda c: f"p{c[1]}-k{int(any(c[2]))}-n{c[3]}")
+def test_every_cell_variant_matches_oracle(g, var, case):
+    """Each FP32 cell-apply variant (2 or 4 vectors per CTA), set explicitly, in both
+    assembly modes: H X (accumulate) and a degree-3 filter (recurrence fused for the
+    cell-interior rows) against the FP64 oracle."""
+    ncell, p, k, nvec = case
+    prob = syn.make_problem(ncell=ncell, h=(1.0, 1.0, 1.0), p=p, k=k, natoms=2, rc=1.2, seed=21)
+    d = fe.Discretisation(prob)
+    X = syn.random_block(d.mesh.nnodes, nvec, 8)
+    c = g.Context(0)
+    c.set_problem(prob)
+    c.set_precision(1)
+    c.set_cell_variant(var)
+    v, vb, nt = c.cell_variant()
+    assert v == var and (vb, nt) == ((4, 512) if var == 4 else (2, 256))
+    Xd = torch.from_numpy(X).to(torch.complex64).cuda()
+    Yd = torch.empty_like(Xd)
+    c.apply_h(Xd, Yd)
+    c.sync_status()
+    assert rel(Yd.cpu().numpy(), d.apply_h(X)) < 1e-5
+    bounds = (1.0, 80.0, -2.0)
+    c.filter(Xd, 3, *bounds)
+    c.sync_status()
+    ref = oc.cheb_filter(d.apply_htilde, X, 3, *bounds)
+    assert rel(Xd.cpu().numpy().astype(np.complex128), ref) < 2e-5
     c.close()
