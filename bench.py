@@ -195,7 +195,7 @@ def CELL_TRAFFIC(nvec, variant):
 # 32 vectors, per cell-apply variant, from the ncu capture in
 # profiles/hx_cell_fused_cube16_p6_nvec32.md; 34 MB of it are the fields (fixed), the rest
 # grows with the vector count
-CELL_TRAFFIC_32 = {2: 1.781e9}
+CELL_TRAFFIC_32 = {2: 1.781e9, 4: 1.786e9}
 
 
 def tc_cell_leg(g, prob, k, X, nvec, peaks, simt_ms):
