@@ -555,7 +555,7 @@ def run_gpu(args):
             peak, peak_src = hbm_peak()
             gbs = by / (ms_t / 1e3) / 1e9
             out["twogrid"] = {
-                "ms": round(ms_t, 4), "kernel": f"k_prolongate<float,{pc + 1},{prob.p + 1},16>",
+                "ms": round(ms_t, 4), "kernel": f"k_prolongate<float,{pc + 1},{prob.p + 1},8>",
                 "algorithmic_bytes": by, "achieved_gbs": round(gbs, 1),
                 "frac_hbm": round(gbs / peak, 4), "peak_gbs": peak, "peak_note": peak_src,
                 "how": f"order {pc} -> {prob.p} on the bench mesh, {nvec} vectors FP32, {nrep} "

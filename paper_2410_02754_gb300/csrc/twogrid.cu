@@ -11,8 +11,11 @@
 //
 // One CTA per (cell, tile of VT vectors), 128 threads = VT vector lanes x G
 // pencil groups, so every global access of a node row is one contiguous
-// VT-vector segment (128 bytes).  Per spin: stage the coarse cell in shared
-// memory, x stage -> B, y stage -> A, z stage -> global.  A cell writes only
+// VT-vector segment (64 bytes: two full 32-byte sectors; the tile is kept this
+// small so that six CTAs fit an SM's shared memory and their gathers overlap).
+// Per spin: stage the coarse cell in shared memory with asynchronous copies
+// (every load of the cell in flight at once, zero-fill for absent nodes),
+// x stage -> B, y stage -> A, z stage -> global.  A cell writes only
 // the fine nodes it owns (local index < p_f in every direction); with the
 // periodic wrap and the Dirichlet faces this writes every free fine node
 // exactly once, with no atomics.  HBM-bound: the coarse block is read and the
@@ -24,6 +27,23 @@ namespace {
 template <typename T, int NC, int NF> struct TwoGridTab {
   T t[NF][NC];   // l^{p_c}_i(x^{p_f}_j)
 };
+
+// asynchronous global -> shared copy of one complex value (8 or 16 bytes);
+// src_bytes = 0 writes zeros
+template <int N>
+__device__ __forceinline__ void cp_async_n(void* dst, const void* src, int src_bytes) {
+  static_assert(N == 8 || N == 16, "8- or 16-byte copies");
+  if (N == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 
 template <typename T, int NC, int NF, int VT>
 __global__ void __launch_bounds__(128)
@@ -47,10 +67,11 @@ k_prolongate(const MeshDev mc, const MeshDev mf, const cplx<T>* __restrict__ Xc,
     for (int i = grp; i < NC * NC * NC; i += G) {
       const int ix = i % NC, iy = (i / NC) % NC, iz = i / (NC * NC);
       const long long I = gbc_node(mc, cx, cy, cz, ix, iy, iz);
-      C u = cmake<C>(0, 0);
-      if (I >= 0 && vok) u = Xc[(I * 2 + s) * ldxc + vec];
-      A[i * VT + v] = u;
+      const bool ok = I >= 0 && vok;
+      cp_async_n<sizeof(C)>(&A[i * VT + v], ok ? &Xc[(I * 2 + s) * ldxc + vec] : Xc,
+                            ok ? (int)sizeof(C) : 0);
     }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
     __syncthreads();
     // x: A [z][y][x] (NC^3) -> B [z][y][xq] (NC^2 NF)
     for (int pid = grp; pid < NC * NC; pid += G) {
@@ -109,7 +130,7 @@ k_prolongate(const MeshDev mc, const MeshDev mf, const cplx<T>* __restrict__ Xc,
   }
 }
 
-template <typename T, int NC, int NF> constexpr int vt_of() { return sizeof(T) == 4 ? 16 : 8; }
+template <typename T, int NC, int NF> constexpr int vt_of() { return sizeof(T) == 4 ? 8 : 4; }
 
 template <typename T, int NC, int NF> constexpr size_t prolongate_smem() {
   constexpr int VT = vt_of<T, NC, NF>();

@@ -1,7 +1,7 @@
 """Two-grid transfer on the GPU (gbc_prolongate, Eq. FEWfnsCMesh) against the FP64 oracle.
 
 * small meshes, element by element, every supported order pair p -> p + 1 (2..7) and p -> p,
-  periodic and Dirichlet faces, FP64 and FP32, ragged vector tiles (16 FP32 / 8 FP64 vectors
+  periodic and Dirichlet faces, FP64 and FP32, ragged vector tiles (8 FP32 / 4 FP64 vectors
   per CTA), padded columns: NaN in the coarse padding (never read) and a sentinel in the fine
   padding (never written);
 * the full cube16_p6 mesh (16^3 cells) from p = 5 to p = 6 on sampled cells, FP32;
