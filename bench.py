@@ -896,6 +896,9 @@ def slab_measure(g, syn, local, nvec, degree, steps, warmup):
         im = torch.rand((M, 2, nvec), generator=gen, dtype=torch.float64, device="cuda") * 2 - 1
         X = torch.complex(re, im).to(dtype)
         del re, im
+        # the FP64 temporaries (up to 112 GB) go back to the driver: the library allocates
+        # its work blocks with cudaMalloc, outside torch's caching allocator
+        torch.cuda.empty_cache()
         return X
 
     def run(prec, dtype, nrep):
