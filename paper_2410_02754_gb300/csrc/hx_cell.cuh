@@ -236,6 +236,7 @@ __device__ __forceinline__ void cell_body(const CellSys* __restrict__ sys, int n
   const int tid = threadIdx.x;
   auto locate = [&](long long it) {
     int q = 0;
+    if (nsys == 1) return q;   // one system: skip the scan over the descriptor slots
 #pragma unroll
     for (int r = 1; r < GBC_MAX_SYS; ++r)
       if (r < nsys && it >= sys[r].item0) q = r;
