@@ -44,3 +44,17 @@ def test_hbm_peak_reads_the_measured_file():
 def test_cell_apply_flop_count():
     assert bench.flops_per_cell_vector(6, 8, True) == 260580
     assert bench.flops_per_cell_vector(6, 8, False) < 260580      # no -i k.grad terms at k = 0
+
+
+def test_cell_traffic_scales_the_captured_variants_only():
+    """roofline.traffic: the DRAM bytes of a captured variant at 32 vectors, the 34 MB of fields
+    fixed and the rest scaled by the vector count; null (with a reason) for a variant that has
+    no capture of the current kernel."""
+    for var, per32 in bench.CELL_TRAFFIC_32.items():
+        t32, _ = bench.CELL_TRAFFIC(32, var)
+        t256, note = bench.CELL_TRAFFIC(256, var)
+        assert abs(t32 - per32) < 1.0
+        assert abs(t256 - (0.034e9 + (per32 - 0.034e9) * 8)) < 1.0 and str(var) in note
+    assert 4 in bench.CELL_TRAFFIC_32             # the variant the tuner picks at p = 6, 256 vectors
+    t, note = bench.CELL_TRAFFIC(256, 0)
+    assert t is None and "no ncu capture" in note
